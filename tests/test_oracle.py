@@ -1,0 +1,341 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix (CPU only).
+
+Each test names the property and the passage it comes from. None of them
+re-types the oracle's own formulas: references are closed forms printed in the
+paper, a textbook potential, an independent brute-force quadrature, exact
+invariances, and identities of the geometry.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_16841_gb300 import inputs
+import _brute
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _appendix_tet(t):
+    h = 10.0 * t
+    return np.array([[h, 0, 0, 0], [0, h, 0, 0], [0, 0, h, 0], [0, 0, 0, 0.0]])
+
+
+def test_appendix_closed_forms():
+    """Appendix example, corner and edge approach (values without 1/(4 pi))."""
+    rows = [l.split() for l in open(os.path.join(GOLD, "appendix_closed_forms.txt")) if not l.startswith("#")]
+    assert len(rows) == 36
+    worst = 0.0
+    for case, t, r, val in rows:
+        t, r, val = float(t), float(r), float(val)
+        eps = r * t
+        x = np.array([t, -eps / math.sqrt(2), -eps / math.sqrt(2), 0.0]) if case == "corner" else \
+            np.array([t, -eps, 5.0 * t, 0.0])
+        got = oracle.inner(x, _appendix_tet(t)) * 4.0 * math.pi
+        rel = abs(got - val) / abs(val)
+        tol = 1e-12 if r < 0.99 else 1e-11   # eps -> t grazes the edge (second derivatives blow up)
+        assert rel < tol, (case, t, r, got, val)
+        worst = max(worst, rel)
+    assert worst < 1e-11
+
+
+def test_appendix_printed_corner_formula_is_inconsistent():
+    """The printed corner formula (eps^2/(4t^2)) misses the exact integral."""
+    t, eps = 1.0, 0.3
+    got = oracle.inner(np.array([t, -eps / math.sqrt(2), -eps / math.sqrt(2), 0.0]), _appendix_tet(t)) * 4 * math.pi
+    printed = (2 * t * (math.pi / 4 - math.asin(eps / (math.sqrt(2) * t))) - math.sqrt(2) * eps * math.log(math.sqrt(2) - 1)
+               + math.sqrt(2) * eps * math.log(math.sqrt(2) * (1 - math.sqrt(1 - eps ** 2 / (4 * t ** 2))) / (eps / t)))
+    assert abs(got - 0.5701562305) < 1e-9
+    assert abs(printed - got) > 0.1
+
+
+def _random_cases(n, seed):
+    m = inputs.sphere_mesh(0, 2, 2.0, 0.2, seed=7)
+    X = m.stv_xyzt()
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        i, j = rng.integers(0, m.n_tet, 2)
+        Ti, tet = X[m.tets[i]], X[m.tets[j]]
+        w = rng.dirichlet([1, 1, 1])
+        x = w[0] * Ti[0] + w[1] * Ti[1] + w[2] * Ti[2]
+        x[0] += rng.uniform(0.2, 1.2)
+        out.append((x, tet))
+    return m, out
+
+
+def test_brute_force_generic_pairs():
+    """P4: oracle against an independent brute-force quadrature."""
+    _, cases = _random_cases(4, 11)
+    for x, tet in cases:
+        ref = _brute.brute_V(x, tet, nsamp=800, npieces=256)
+        got = oracle.inner(x, tet)
+        assert abs(got - ref) <= 1e-9 * max(abs(ref), 1e-3), (got, ref)
+
+
+def test_brute_force_in_plane_and_near_plane():
+    """P4: apex in the panel plane (d = 0), just above it, and on a panel face."""
+    m = inputs.sphere_mesh(0, 3, 1.5, 0.2, seed=3)
+    X = m.stv_xyzt()
+    tet = X[m.tets[4]]
+    P = tet[:, 1:]
+    cen = P.mean(axis=0)
+    n = np.cross(P[1] - P[0], P[2] - P[0])
+    n /= np.linalg.norm(n)
+    for dz, dt in [(0.0, 0.35), (1e-8, 0.35), (0.05, 0.4)]:
+        x = np.concatenate([[tet[:, 0].mean() + dt], cen + dz * n + 0.03 * (P[0] - cen)])
+        ref = _brute.brute_V(x, tet, nsamp=800, npieces=256)
+        got = oracle.inner(x, tet)
+        assert abs(got - ref) <= 1e-9 * max(abs(ref), 1e-3), (dz, got, ref)
+    # apex on a face of the panel itself (coincident pair)
+    x = 0.2 * tet[0] + 0.3 * tet[1] + 0.5 * tet[2]
+    ref = _brute.brute_V(x, tet, nsamp=800, npieces=256)
+    got = oracle.inner(x, tet)
+    assert abs(got - ref) <= 1e-9 * max(abs(ref), 1e-3)
+
+
+def test_static_limit_laplace_triangle():
+    """P2: a whole time column over K sums to the Laplace single layer of K.
+
+    With max_K |x-y| < t < T + min_K |x-y| the cone cuts the column over its full
+    spatial extent, so sum_j V 1_sigma_j (x) = 1/(4pi) int_K dA/|x-y|.
+    """
+    m = inputs.sphere_mesh(0, 6, 3.0, 0.2, seed=5)
+    X = m.stv_xyzt()
+    col = np.arange(0, 3 * 6)            # first spatial triangle, all slabs
+    tri = m.svert[np.sort(m.tri[0])]
+    cen = tri.mean(axis=0)
+    n = np.cross(tri[1] - tri[0], tri[2] - tri[0])
+    n /= np.linalg.norm(n)
+    for off in [np.array([0.2, 0.1, 0.05]), 0.3 * n + 0.02, 0.01 * n]:
+        xs = cen + off
+        dmax = max(np.linalg.norm(xs - p) for p in tri)
+        x = np.concatenate([[dmax + 0.7], xs])
+        s = sum(oracle.inner(x, X[m.tets[j]]) for j in col)
+        ref = _brute.laplace_triangle(xs, tri)
+        assert abs(s - ref) <= 1e-13 * abs(ref) + 1e-15, (s, ref)
+
+
+def test_exact_zeros_outside_pattern():
+    """P6: entries outside the causal / Huygens / reach pattern are exactly 0.0."""
+    m = inputs.sphere_mesh(0, 3, 2.0, 0.2, seed=9)
+    om = oracle.Mesh.from_spacetime(m)
+    P = om.pattern()
+    rng = np.random.default_rng(0)
+    out = np.argwhere(P == 0)
+    pick = out[rng.choice(out.shape[0], 1500, replace=False)]
+    v = om.entries(pick, use_pattern=False, nthreads=os.cpu_count())
+    assert np.all(v == 0.0)
+    inn = np.argwhere(P != 0)
+    pick = inn[rng.choice(inn.shape[0], 300, replace=False)]
+    v = om.entries(pick, nthreads=os.cpu_count())
+    assert np.count_nonzero(v) > 150
+
+
+def test_panel_geometry_identities():
+    """Eq. pnl_ilf: conormals lie in the panel hyperplane, are unit and outward;
+    the divergence theorem in the hyperplane gives sum_F nu_{F,t}|F| = 0 and
+    sum_F nu_{F,t} int_F tau dS = |sigma|."""
+    m = inputs.sphere_mesh(1, 2, 2.0, 0.2, seed=1)
+    X = m.stv_xyzt()
+    for j in [0, 5, 100, 477]:
+        tet = X[m.tets[j]]
+        nu, cn, area, vol = oracle.tet_geometry(tet)
+        assert nu[0] == 0.0                       # flat in Gamma_K x R
+        for i in range(4):
+            assert abs(np.dot(cn[i], nu)) < 1e-14
+            assert abs(np.linalg.norm(cn[i]) - 1) < 1e-14
+            fc = np.mean([tet[k] for k in range(4) if k != i], axis=0)
+            assert np.dot(tet[i] - fc, cn[i]) < 0  # vertex i lies inside
+        assert abs(np.sum(cn[:, 0] * area)) < 1e-14
+        tau_mean = np.array([np.mean([tet[k, 0] for k in range(4) if k != i]) for i in range(4)])
+        # independent 3-volume: Gram determinant of the edge vectors
+        E = tet[1:] - tet[0]
+        vol_ref = math.sqrt(np.linalg.det(E @ E.T)) / 6.0
+        assert abs(np.sum(cn[:, 0] * area * tau_mean) - vol_ref) < 1e-14
+        assert abs(vol - vol_ref) < 1e-14
+
+
+def test_midpoint_rule():
+    """Fig. int_tri_mid: m^2 centroids of congruent sub-triangles; exact for
+    linear functions, so the point mean is the centroid (1/3, 1/3)."""
+    assert np.allclose(oracle.midpoint_rule(1), [[1 / 3, 1 / 3]])
+    for m in [1, 2, 3, 5]:
+        xi = oracle.midpoint_rule(m)
+        assert xi.shape == (m * m, 2)
+        assert np.allclose(xi.mean(axis=0), [1 / 3, 1 / 3], atol=1e-15)
+        assert len({tuple(np.round(p, 12)) for p in xi}) == m * m
+        assert np.all(xi.sum(axis=1) < 1.0)
+    # m = 2: three corner sub-triangles and the central (downward) one
+    xi = sorted(map(tuple, np.round(oracle.midpoint_rule(2), 12)))
+    ref = sorted([(1 / 6, 1 / 6), (1 / 6, 2 / 3), (2 / 3, 1 / 6), (1 / 3, 1 / 3)])
+    assert np.allclose(xi, ref)
+
+
+def test_time_translation_invariance():
+    """P7: on uniform slabs the matrix is block Toeplitz in the slab index."""
+    m = inputs.sphere_mesh(0, 4, 2.0, 0.0)
+    om = oracle.Mesh.from_spacetime(m)
+    ns = 4
+    rng = np.random.default_rng(1)
+    pairs, shifted = [], []
+    for _ in range(60):
+        ci, cj = rng.integers(0, 20, 2)
+        n, k = rng.integers(0, ns - 1), rng.integers(0, 3)
+        mm, kk = rng.integers(0, n + 1), rng.integers(0, 3)
+        i, j = (ci * ns + n) * 3 + k, (cj * ns + mm) * 3 + kk
+        pairs.append((i, j))
+        shifted.append((i + 3, j + 3))
+    a = om.entries(pairs, nthreads=os.cpu_count())
+    b = om.entries(shifted, nthreads=os.cpu_count())
+    scale = np.abs(a).max()
+    assert scale > 0
+    assert np.max(np.abs(a - b)) <= 1e-13 * scale
+
+
+def test_space_time_scaling():
+    """P8: scaling space and time by lam scales V by lam and entries by lam^3."""
+    m = inputs.sphere_mesh(0, 3, 2.0, 0.2, seed=4)
+    X = m.stv_xyzt()
+    om = oracle.Mesh(X, m.stv_sv, m.tets)
+    om2 = oracle.Mesh(2.0 * X, m.stv_sv, m.tets)
+    P = om.pattern()
+    rng = np.random.default_rng(2)
+    ij = np.argwhere(P)[rng.choice(int(P.sum()), 80, replace=False)]
+    a = om.entries(ij, nthreads=os.cpu_count())
+    b = om2.entries(ij, nthreads=os.cpu_count())
+    assert np.max(np.abs(b - 8.0 * a)) <= 1e-13 * np.abs(a).max()
+
+
+def test_rotation_invariance():
+    """P8: a rotation of the whole mesh leaves every entry unchanged."""
+    m = inputs.sphere_mesh(0, 3, 2.0, 0.2, seed=4)
+    X = m.stv_xyzt()
+    th = 0.7
+    Rz = np.array([[math.cos(th), -math.sin(th), 0], [math.sin(th), math.cos(th), 0], [0, 0, 1.0]])
+    X2 = X.copy()
+    X2[:, 1:] = X[:, 1:] @ Rz.T
+    om, om2 = oracle.Mesh(X, m.stv_sv, m.tets), oracle.Mesh(X2, m.stv_sv, m.tets)
+    rng = np.random.default_rng(3)
+    P = om.pattern()
+    ij = np.argwhere(P)[rng.choice(int(P.sum()), 60, replace=False)]
+    a = om.entries(ij, nthreads=os.cpu_count())
+    b = om2.entries(ij, nthreads=os.cpu_count())
+    assert np.max(np.abs(a - b)) <= 1e-13 * np.abs(a).max()
+
+
+def test_rhs_against_direct_face_integrals():
+    """Eq. int_bform with A = Id: b_i = -sum_F nu_{F,t} int_F g dS. For a panel
+    between the graphs tau = P_lo(y) and tau = P_hi(y) over K this equals
+    int_K [g(P_lo(y), y) - g(P_hi(y), y)] dA, integrated here by scipy."""
+    from scipy import integrate
+    m = inputs.sphere_mesh(0, 3, 2.0, 0.2, seed=6)
+    om = oracle.Mesh.from_spacetime(m)
+    prm = inputs.pulse_params(2, seed=2)
+    b0 = om.rhs(inputs.DATA_SIN2_UNIFORM)
+    b1 = om.rhs(inputs.DATA_PULSE, prm)
+    X = m.stv_xyzt()
+
+    def g0(t, y):
+        return math.sin(0.5 * math.pi * t) ** 2 if 0 < t < 2 else 0.0
+
+    def g1(t, y, p):
+        return math.exp(-((t - np.dot(y, p[:3]) - p[3]) / p[4]) ** 2)
+
+    for i in [0, 7, 31, 50]:
+        V = X[m.tets[i]]
+        sv = m.stv_sv[m.tets[i]]
+        # corners: the three distinct spatial vertices; lower/upper times there
+        corners = sorted(set(sv))
+        P = np.array([m.svert[c] for c in corners])
+        lo = np.array([min(V[k, 0] for k in range(4) if sv[k] == c) for c in corners])
+        hi = np.array([max(V[k, 0] for k in range(4) if sv[k] == c) for c in corners])
+        area = 0.5 * np.linalg.norm(np.cross(P[1] - P[0], P[2] - P[0]))
+
+        def integrand(v, u, g):
+            w = np.array([1 - u - v, u, v])
+            y = w @ P
+            return 2 * area * (g(w @ lo, y) - g(w @ hi, y))
+
+        for kind, bb, gs in [(0, b0[:, 0], [g0]), (1, b1, [lambda t, y, p=prm[0]: g1(t, y, p),
+                                                             lambda t, y, p=prm[1]: g1(t, y, p)])]:
+            for r, g in enumerate(gs):
+                ref, _ = integrate.dblquad(lambda v, u: integrand(v, u, g), 0, 1, 0, lambda u: 1 - u,
+                                           epsabs=1e-14, epsrel=1e-12)
+                got = bb[i] if bb.ndim == 1 else bb[i, r]
+                assert abs(got - ref) <= 1e-11 * max(abs(ref), 2e-3), (i, kind, r, got, ref)
+
+
+def test_lemma_chart_integrand_is_r0():
+    """Lemma kernel_para with the chart l_2 of Sec. 3.1: k_{psi,1}(l_2) J_{l_2} = r0.
+
+    J_{l_2} is the surface element of l_2(rho, phi) = (rho, phi, arccos(rho0/rho))
+    in parameter space, taken here by finite differences."""
+    r0 = 1.7
+    for rho0 in [0.0, 0.2, -0.35]:
+        for rho in [abs(rho0) + 0.05, 0.5, 0.93]:
+            th = math.acos(rho0 / rho)
+            k = r0 * rho * math.sin(th) / math.sqrt(math.cos(th) ** 2 + (rho * math.sin(th)) ** 2)
+            h = 1e-6
+            dth = (math.acos(rho0 / (rho + h)) - math.acos(rho0 / (rho - h))) / (2 * h)
+            J = math.sqrt(1.0 + dth * dth)      # |d l2/d rho x d l2/d phi|
+            assert abs(k * J - r0) < 1e-8
+
+
+def test_theorem_ball_bounds():
+    """P9, Theorem phi_xi_sphere: min/max of phi_Xi(x - z) over a 4D ball."""
+    rng = np.random.default_rng(8)
+    for _ in range(40):
+        x = rng.normal(size=4)
+        y = rng.normal(size=4)
+        r = rng.uniform(0.05, 1.5)
+        a = np.linalg.norm(x[1:] - y[1:])
+        phi = a - (x[0] - y[0])
+        dr = a + math.sqrt(r * r - a * a) if a < r / math.sqrt(2) else r * math.sqrt(2)
+        z = rng.normal(size=(20000, 4))
+        z = y + r * z / np.linalg.norm(z, axis=1, keepdims=True) * rng.uniform(0, 1, (20000, 1)) ** 0.25
+        vals = np.linalg.norm(x[1:] - z[:, 1:], axis=1) - (x[0] - z[:, 0])
+        assert vals.min() >= phi - dr - 1e-12
+        assert vals.max() <= phi + r * math.sqrt(2) + 1e-12
+        # extremal points printed in the proof attain the bounds
+        u = (x[1:] - y[1:]) / a
+        zmax = y - r / math.sqrt(2) * np.concatenate([[-1.0], u])
+        assert abs(np.linalg.norm(x[1:] - zmax[1:]) - (x[0] - zmax[0]) - (phi + r * math.sqrt(2))) < 1e-12
+        if a >= r / math.sqrt(2):
+            zmin = y + r / math.sqrt(2) * np.concatenate([[-1.0], u])
+        else:
+            zmin = np.concatenate([[y[0] - math.sqrt(r * r - a * a)], x[1:]])
+        assert abs(np.linalg.norm(x[1:] - zmin[1:]) - (x[0] - zmin[0]) - (phi - dr)) < 1e-12
+
+
+def test_sphere_closed_form_coarse():
+    """P1 (discretisation level): on the sphere, V phi = 1/2 int_0^min(t,2) phi(t-r) dr
+    for uniform phi; g = sin^2(pi t/2) on [0,2] has phi = pi sin(pi t). On the
+    20-triangle icosahedron (edge ~ 1.05) the Galerkin solution follows it in
+    sign and shape with an L2(Sigma) error near 0.46; the finer levels are
+    checked on the GPU, where the error must fall with h."""
+    m = inputs.sphere_mesh(0, 4, 2.0, 0.0)
+    om = oracle.Mesh.from_spacetime(m)
+    A = om.matrix(nthreads=os.cpu_count())
+    b = om.rhs(inputs.DATA_SIN2_UNIFORM)[:, 0]
+    w = oracle.lu_solve(A, b)
+    X = m.stv_xyzt()
+    # L2(Sigma) error with a 3-point-in-time rule per panel (phi depends on t only)
+    err2 = ref2 = 0.0
+    for j in range(m.n_tet):
+        tet = X[m.tets[j]]
+        _, _, _, vol = oracle.tet_geometry(tet)
+        ts = tet[:, 0]
+        # degree-2 tetrahedral rule (Keast 4-point) on the barycentric simplex
+        a, bq = 0.5854101966249685, 0.1381966011250105
+        for k in range(4):
+            lam = np.full(4, bq)
+            lam[k] = a
+            tq = lam @ ts
+            ex = math.pi * math.sin(math.pi * tq)
+            err2 += vol / 4 * (ex - w[j]) ** 2
+            ref2 += vol / 4 * ex ** 2
+    e = math.sqrt(err2 / ref2)
+    assert e < 0.55, e
