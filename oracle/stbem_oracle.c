@@ -182,10 +182,15 @@ static int face_roots(const inner_ctx* c, int i, double beta, double lo, double 
   int nc = 0;
   double scale = fabs(al) + fabs(beta) + fabs(ga);
   if (scale == 0.0) return 0;
-  if (fabs(a) <= 1e-15 * (al * al + beta * beta)) {
+  if (fabs(beta) <= 1e-15 * (fabs(al) + fabs(ga))) {
+    /* face with a purely temporal conormal: f_i is linear in rho */
+    if (al != 0.0) cand[nc++] = ga / al;
+  } else if (fabs(a) <= 1e-15 * (al * al + beta * beta)) {
     if (b != 0.0) cand[nc++] = -cc / b;
   } else {
     double disc = b * b - 4.0 * a * cc;
+    /* a double root may round to a slightly negative discriminant */
+    if (disc < 0.0 && disc > -1e-13 * b * b) disc = 0.0;
     if (disc < 0.0) return 0;
     double sq = sqrt(disc);
     double q = -0.5 * (b + (b >= 0 ? sq : -sq));

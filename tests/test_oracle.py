@@ -339,3 +339,19 @@ def test_sphere_closed_form_coarse():
             ref2 += vol / 4 * ex ** 2
     e = math.sqrt(err2 / ref2)
     assert e < 0.55, e
+
+
+def test_brute_force_apex_above_flat_top_face():
+    """P4: apex in the panel plane above a face of constant time (the face
+    t = T). That face's function in eq. dist_faces is linear in rho; its root
+    bounds the lit set (the cone above the face is outside the panel)."""
+    m = inputs.sphere_mesh(1, 4, 2.0, 0.2, seed=3)
+    X = m.stv_xyzt()
+    for j, w, dt in [(947, (0.2, 0.5, 0.3), 0.0014), (539, (0.6, 0.1, 0.3), 0.17)]:
+        tet = X[m.tets[j]]
+        x = w[0] * tet[0] + w[1] * tet[1] + w[2] * tet[2]
+        x[0] = 2.0 + dt
+        ref = _brute.brute_V(x, tet, nsamp=800, npieces=256)
+        got = oracle.inner(x, tet)
+        assert ref > 0.0
+        assert abs(got - ref) <= 1e-9 * max(abs(ref), 1e-3), (j, got, ref)
