@@ -1,0 +1,236 @@
+/*
+ * stbem.h - C ABI of the GB300 space-time Galerkin BEM library for the
+ * retarded single layer of the 3D wave equation (Poelz & Schanz, "On the
+ * space-time discretization of variational retarded potential boundary
+ * integral equations").
+ *
+ * Problem (Sec. 2, eq. pde/ic/bc and Table bie, indirect method): given the
+ * lateral boundary Sigma = (0,T) x Gamma, meshed by flat space-time
+ * tetrahedra ("panels", Sec. 3), and Dirichlet data g, find the density
+ * w_h in S_h^0 (one value per panel, Def. st_be) with
+ *     b_V(w_h, v_h) = b_I(g, v_h)   for all v_h in S_h^0      (eq. df_ind),
+ * where b_A(w, v_h) = -sum_sigma int_{d sigma} nu_{d sigma,t} v_h A w dS
+ * (eq. int_bform), V is the retarded single layer operator (eq. slp) and the
+ * face integrals use the composite midpoint rule of Fig. int_tri_mid.
+ *
+ * Conventions for every call:
+ *   - Every call returns a bem_status; no C++ exception crosses the ABI.
+ *     bem_last_error() gives a thread-local description of the last failure.
+ *   - Pointers are host pointers unless a name says "dev" or the call takes a
+ *     stream; device pointers must be on the context's device.
+ *   - Inputs are copied; the caller keeps ownership of its arrays. Outputs are
+ *     caller-allocated. Handles are opaque and released by their destroy call.
+ *   - Panels, matrix rows/columns and vector entries use the caller's panel
+ *     numbering (the order of `tets`); multi-vector arrays are column-major
+ *     [n_tet x nrhs] (entry (i, r) at i + n_tet * r).
+ *   - All computation runs in CUDA kernels on the GPU; there is no CPU path.
+ *     A call made without a usable GPU returns BEM_ERR_CUDA.
+ */
+#ifndef STBEM_H
+#define STBEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BEM_OK = 0,
+  BEM_ERR_INVALID_ARG = 1,   /* null pointer, negative size, unknown enum */
+  BEM_ERR_OUT_OF_MEMORY = 2, /* device or host allocation failed */
+  BEM_ERR_CUDA = 3,          /* a CUDA runtime call failed (no GPU, launch error) */
+  BEM_ERR_NOT_CONVERGED = 4, /* solver stopped at maxit; best iterate returned */
+  BEM_ERR_DEVICE_TIMEOUT = 5,/* a bounded device wait gave up */
+  BEM_ERR_UNSUPPORTED = 6,   /* option or mesh shape outside what is built */
+  BEM_ERR_BAD_MESH = 7,      /* mesh fails validation (see bem_mesh_create) */
+  BEM_ERR_INTERNAL = 8
+} bem_status;
+
+typedef struct bem_context bem_context;
+typedef struct bem_mesh bem_mesh;
+typedef struct bem_operator bem_operator;
+
+/* Precision of the panel-pair quadrature.
+ *  FP64 : every step in double precision.
+ *  MIXED: light-cone / panel intersection geometry (distances, cone-function
+ *         values at vertices, crossing points) in double; the conic-arc
+ *         quadrature and the closed-form edge terms in single precision. */
+enum { BEM_PREC_FP64 = 0, BEM_PREC_MIXED = 1 };
+
+/* Storage precision of assembled matrix values used by matvec / inner solves. */
+enum { BEM_DTYPE_FP64 = 0, BEM_DTYPE_FP32 = 1 };
+
+/* Dirichlet data families (evaluated at space-time points (t, x)):
+ *  BEM_DATA_SIN2_UNIFORM: g = sin^2(pi t / 2) for 0 < t < 2, else 0
+ *                         (params ignored);
+ *  BEM_DATA_PULSE       : g = exp(-((t - <x, d> - c) / w)^2), params per
+ *                         right-hand side: (d0, d1, d2, c, w). */
+enum { BEM_DATA_SIN2_UNIFORM = 0, BEM_DATA_PULSE = 1 };
+
+/* ------------------------------------------------------------------ */
+/* Context                                                              */
+/* ------------------------------------------------------------------ */
+
+/* Binds CUDA device `device` (usually 0) and creates the streams the library
+ * uses. Fails with BEM_ERR_CUDA when no device is usable. */
+bem_status bem_context_create(int device, bem_context** out);
+void bem_context_destroy(bem_context* ctx);
+/* Thread-local text of the last failure in this thread ("" if none). */
+const char* bem_last_error(void);
+const char* bem_version(void);
+
+/* ------------------------------------------------------------------ */
+/* Space-time mesh of Sigma (Sec. 3: Sigma_N of open tetrahedra)        */
+/* ------------------------------------------------------------------ */
+
+/* General space-time tetrahedral mesh.
+ *   sv_xyz [n_sv][3]  spatial vertices (points of Gamma's triangulation)
+ *   stv_sv [n_stv]    spatial vertex of each space-time vertex
+ *   stv_t  [n_stv]    time of each space-time vertex
+ *   tets   [n_tet][4] space-time vertex ids of each panel
+ * Each panel must be flat in Gamma_K x R for a flat spatial triangle K: its
+ * four vertices lie over the three corners of K, two of them over the same
+ * spatial vertex (a vertical edge) with different times; K must be
+ * non-degenerate. The two faces containing the vertical edge have
+ * nu_{F,t} = 0 (decided on vertex ids, never on floating point) and drop out
+ * of eq. int_bform; the other two faces are graphs tau = P(y) over K.
+ * Violations return BEM_ERR_BAD_MESH. At most 192 panels may share one
+ * spatial triangle (BEM_ERR_UNSUPPORTED beyond). */
+bem_status bem_mesh_create(bem_context* ctx, int64_t n_sv, const double* sv_xyz, int64_t n_stv,
+                           const int32_t* stv_sv, const double* stv_t, int64_t n_tet, const int32_t* tets,
+                           bem_mesh** out);
+
+/* Prism mesh convenience builder: triangles tri [n_tri][3] of Gamma, per
+ * spatial vertex the time nodes time_nodes [n_sv][n_slabs+1] (increasing).
+ * Each prism K x [t_n, t_{n+1}] is split into three panels by the sorted
+ * vertex-id rule (vertices a<b<c): {a_n,b_n,c_n,a_{n+1}}, {b_n,c_n,a_{n+1},b_{n+1}},
+ * {c_n,a_{n+1},b_{n+1},c_{n+1}}; panel (k, n, s) gets number (k*n_slabs+n)*3+s. */
+bem_status bem_mesh_create_prisms(bem_context* ctx, int64_t n_sv, const double* sv_xyz, int64_t n_tri,
+                                  const int32_t* tri, int32_t n_slabs, const double* time_nodes,
+                                  bem_mesh** out);
+
+/* Sizes: panels, spatial triangles ("columns"), distinct nu_t != 0 faces. */
+bem_status bem_mesh_info(const bem_mesh* mesh, int64_t* n_tet, int64_t* n_columns, int64_t* n_surfaces);
+void bem_mesh_destroy(bem_mesh* mesh);
+
+/* ------------------------------------------------------------------ */
+/* Operator: the Galerkin matrix A_ij = b_V(1_{sigma_j}, 1_{sigma_i})    */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  int32_t precision; /* BEM_PREC_FP64 or BEM_PREC_MIXED */
+  int32_t m_q;       /* midpoint-rule subdivision m_Q (Fig. int_tri_mid); 1..8, paper uses 3 */
+  int32_t n_theta;   /* cap on Gauss nodes per conic-arc piece (4..32); 0 = default (32 FP64, 16 MIXED).
+                        The count per piece is chosen from the distance of the integrand's nearest
+                        complex pole to reach 1e-15 (FP64) or 1e-7 (MIXED) relative accuracy. */
+  int32_t store_fp32;/* 1: also keep an FP32 copy of the values for low-precision matvecs */
+} bem_op_opts;
+
+/* Assembles the sparse Galerkin matrix on the device.
+ *   A_ij = -sum_{F in faces(sigma_i), nu_{F,t} != 0} nu_{F,t} |F|/m_Q^2
+ *          * sum_q V 1_{sigma_j}(x_{F,q})                 (eq. int_bform, Fig. int_tri_mid)
+ * with the inner value V 1_sigma(x) of eq. tk_para (exact up to the conic-arc
+ * rule). Entry (i,j) is in the sparsity pattern when some outer point x_{F,q}
+ * of panel i can see panel j on its backward light cone: causality
+ * (Def. choice_r), the strong Huygens principle (the panel is not strictly
+ * inside the cone) and the ball bound of Theorem phi_xi_sphere; entries
+ * outside the pattern are exactly 0.0. The pattern decisions are made in
+ * FP64 with the operation order of the published contract (bit-exact). */
+bem_status bem_operator_create(bem_context* ctx, const bem_mesh* mesh, const bem_op_opts* opts,
+                               bem_operator** out);
+
+/* nnz_pattern: pattern entries; stored_values: values kept (band padding
+ * included); n_blocks: stored (column, column) blocks; assemble_ms: device
+ * time of the last assembly. Any pointer may be NULL. */
+bem_status bem_operator_stats(const bem_operator* op, int64_t* nnz_pattern, int64_t* stored_values,
+                              int64_t* n_blocks, double* assemble_ms);
+
+/* Device time of the last assembly by phase (CUDA events on the assembly
+ * stream): ms[0] outer points, ms[1] sparsity pattern pass, ms[2] block
+ * offsets (host scan), ms[3] quadrature + assembly pass. */
+bem_status bem_operator_timings(const bem_operator* op, double* ms);
+
+/* Re-runs pattern + quadrature + assembly on the existing operator (same
+ * mesh and options) on `stream` (NULL: the context stream). Used to time
+ * assembly passes; the values are overwritten with identical results. */
+bem_status bem_operator_reassemble(bem_operator* op, void* stream);
+
+/* Pattern rows in the caller's numbering, CSR with ascending columns.
+ * rowptr [n_tet+1] (int64), cols [nnz_pattern]. */
+bem_status bem_operator_export_pattern(const bem_operator* op, int64_t* rowptr, int32_t* cols);
+
+/* Dense matrix (row-major [n_tet][n_tet]); for small meshes (n_tet <= 20000). */
+bem_status bem_operator_export_dense(const bem_operator* op, double* A);
+
+/* Values A_ij for a list of pairs ij [n][2] (caller numbering). Pairs
+ * outside the pattern give exactly 0.0. */
+bem_status bem_operator_entries(const bem_operator* op, int64_t n, const int32_t* ij, double* out);
+
+void bem_operator_destroy(bem_operator* op);
+
+/* ------------------------------------------------------------------ */
+/* Right-hand side b_i = b_I(g, 1_{sigma_i}) = -sum_F nu_{F,t} int_F g dS */
+/* (eq. int_bform with A = Id), Duffy-collapsed 10x10 Gauss per face.   */
+/* ------------------------------------------------------------------ */
+
+/* params [nrhs][5] for BEM_DATA_PULSE (NULL for SIN2_UNIFORM); b host
+ * [n_tet x nrhs] column-major. */
+bem_status bem_rhs(const bem_operator* op, int32_t kind, int32_t nrhs, const double* params, double* b);
+
+/* ------------------------------------------------------------------ */
+/* Matrix-vector products                                               */
+/* ------------------------------------------------------------------ */
+
+/* y_dev = A x_dev for nrhs column-major vectors in FP64 (device pointers),
+ * enqueued on `stream` (a cudaStream_t; NULL = context stream). */
+bem_status bem_matvec(const bem_operator* op, const double* x_dev, double* y_dev, int32_t nrhs, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Solve eq. df_ind (the paper names no linear solver: restarted GMRES)  */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  double tol;          /* relative residual ||b - A w|| / ||b|| target */
+  int32_t restart;     /* GMRES restart length m (1..200) */
+  int32_t maxit;       /* max total inner iterations per right-hand side */
+  int32_t inner_dtype; /* BEM_DTYPE_FP64 or BEM_DTYPE_FP32 (then FP64 refinement) */
+  int32_t max_refine;  /* outer refinement steps when inner_dtype != FP64 */
+} bem_solve_opts;
+
+typedef struct {
+  int32_t iterations;  /* total GMRES iterations (all refinement steps) */
+  int32_t refinements; /* outer refinement steps taken */
+  int32_t converged;   /* 1 if tol was met */
+  int32_t reserved;
+  double rel_residual; /* final FP64 relative residual */
+  double solve_ms;     /* wall time of the solve on the device */
+} bem_solve_info;
+
+/* Host arrays b, w [n_tet x nrhs]; info [nrhs] may be NULL. Zero initial
+ * guess. Returns BEM_ERR_NOT_CONVERGED (with the best iterate in w) when a
+ * right-hand side misses tol. */
+bem_status bem_solve(bem_operator* op, const double* b, double* w, int32_t nrhs, const bem_solve_opts* opts,
+                     bem_solve_info* info);
+
+/* Same on device arrays, enqueued on `stream`; blocks until done. */
+bem_status bem_solve_device(bem_operator* op, const double* b_dev, double* w_dev, int32_t nrhs,
+                            const bem_solve_opts* opts, bem_solve_info* info, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Kernel-level entry: inner integral for arbitrary (point, panel) pairs */
+/* ------------------------------------------------------------------ */
+
+/* out[k] = V 1_{sigma_k}(x_k) = (1/4pi) int_{K_k} 1[(t - |x-y|, y) in sigma_k] / |x-y| dA
+ * (eq. slp with the delta integrated, i.e. T_{k_1} of eq. tk_para), for host
+ * arrays x4 [n][4] = (t,x,y,z), tets [n][4][4] vertex coordinates (t,x,y,z),
+ * tet_sv [n][4] spatial-vertex ids (equal ids mark the vertical edge).
+ * precision and n_theta as in bem_op_opts. */
+bem_status bem_inner_potentials(bem_context* ctx, int64_t n, const double* x4, const double* tets,
+                                const int32_t* tet_sv, int32_t precision, int32_t n_theta, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STBEM_H */

@@ -30,7 +30,8 @@
  *     with the composite midpoint rule of Fig. int_tri_mid (m_Q^2 congruent
  *     sub-triangles, one centroid each);
  *   - the right-hand side b_I(g, v_h) = -sum_F nu_{F,t} int_F g dS of
- *     eq. int_bform with A = Id, by a Duffy-collapsed Gauss-Legendre rule;
+ *     eq. int_bform with A = Id, by a composite Duffy-collapsed Gauss rule
+ *     fine enough to resolve the data;
  *   - the sparsity predicate (causality, strong Huygens principle, spatial
  *     reach) in a fixed FP64 operation order;
  *   - dense LU with partial pivoting.
@@ -84,7 +85,7 @@ static pthread_once_t rules_once = PTHREAD_ONCE_INIT;
 static void init_rules(void) {
   gauss_legendre(10, &G_LO);
   gauss_legendre(16, &G_HI);
-  gauss_legendre(16, &G_FACE);
+  gauss_legendre(12, &G_FACE);
 }
 
 /* ------------------------------------------------------------------ */
@@ -689,35 +690,70 @@ static double data_g(int kind, const double* prm, const double* x) {
   return exp(-a * a);
 }
 
-/* b[i + n_tet*r] = -sum_F nu_{F,t} int_F g_r dS, Duffy-collapsed 16x16 Gauss */
+/* int over the 4D face triangle (A, B, C) of g: the face is split into m^2
+ * congruent sub-triangles (the same subdivision as Fig. int_tri_mid), each
+ * integrated by a Duffy-collapsed 12 x 12 Gauss-Legendre rule. */
+static double face_integral(const double* A, const double* B, const double* C, double area, int m, int kind,
+                            const double* prm) {
+  const gauss_rule* G = &G_FACE;
+  double tot = 0.0;
+  for (int p = 0; p < m; ++p)
+    for (int q = 0; p + q < m; ++q)
+      for (int down = 0; down < 2; ++down) {
+        double b0[2], b1[2], b2[2]; /* (xi1, xi2) of the sub-triangle corners */
+        if (!down) {
+          b0[0] = (double)p / m; b0[1] = (double)q / m;
+          b1[0] = (double)(p + 1) / m; b1[1] = (double)q / m;
+          b2[0] = (double)p / m; b2[1] = (double)(q + 1) / m;
+        } else {
+          if (p + q + 2 > m) continue;
+          b0[0] = (double)(p + 1) / m; b0[1] = (double)q / m;
+          b1[0] = (double)(p + 1) / m; b1[1] = (double)(q + 1) / m;
+          b2[0] = (double)p / m; b2[1] = (double)(q + 1) / m;
+        }
+        for (int a = 0; a < G->n; ++a) {
+          double u = 0.5 * (G->x[a] + 1.0), wu = 0.5 * G->w[a];
+          for (int c = 0; c < G->n; ++c) {
+            double v = 0.5 * (G->x[c] + 1.0), wv = 0.5 * G->w[c];
+            double x1 = (1.0 - u) * b0[0] + u * (1.0 - v) * b1[0] + u * v * b2[0];
+            double x2 = (1.0 - u) * b0[1] + u * (1.0 - v) * b1[1] + u * v * b2[1];
+            double x[4];
+            for (int d = 0; d < 4; ++d) x[d] = A[d] + x1 * (B[d] - A[d]) + x2 * (C[d] - A[d]);
+            tot += wu * wv * u * data_g(kind, prm, x);
+          }
+        }
+      }
+  return 2.0 * area / ((double)m * m) * tot;
+}
+
+/* b[i + n_tet*r] = -sum_F nu_{F,t} int_F g_r dS. The subdivision level makes
+ * a sub-triangle span at most a quarter of the data's length scale (pulse
+ * width w; 0.5 for the sin^2 data). */
 int orc_rhs(int n_stv, const double* X, const int* sv, int n_tet, const int* tets, int kind,
             int nrhs, const double* params, double* b) {
   pthread_once(&rules_once, init_rules);
   orc_mesh m = {n_stv, X, sv, n_tet, tets};
-  const gauss_rule* G = &G_FACE;
   for (int i = 0; i < n_tet; ++i) {
     double Xi[4][4];
     tet_vertices(&m, i, Xi);
     tet_geom g;
     tet_geometry(Xi, &g);
+    double diam = 0.0;
+    for (int a = 0; a < 4; ++a)
+      for (int c = a + 1; c < 4; ++c) {
+        double dd = dist3(Xi[a] + 1, Xi[c] + 1);
+        if (dd > diam) diam = dd;
+      }
     for (int r = 0; r < nrhs; ++r) {
       const double* prm = params ? params + 5 * r : NULL;
+      double scale = kind == 1 ? 0.25 * prm[4] : 0.25;
+      int msub = 1;
+      while (msub < 64 && diam / msub > scale) msub *= 2;
       double sum = 0.0;
       for (int k = 0; k < 4; ++k) {
         if (face_is_vertical(&m, i, k)) continue;
         int a = (k + 1) % 4, bb = (k + 2) % 4, c = (k + 3) % 4;
-        double s = 0.0;
-        for (int p = 0; p < G->n; ++p) {
-          double u = 0.5 * (G->x[p] + 1.0), wu = 0.5 * G->w[p];
-          for (int q = 0; q < G->n; ++q) {
-            double v = 0.5 * (G->x[q] + 1.0), wv = 0.5 * G->w[q];
-            double x[4];
-            for (int d = 0; d < 4; ++d)
-              x[d] = Xi[a][d] + u * (Xi[bb][d] - Xi[a][d]) + u * v * (Xi[c][d] - Xi[bb][d]);
-            s += wu * wv * u * data_g(kind, prm, x);
-          }
-        }
-        sum += -g.cn[k][0] * 2.0 * g.area[k] * s;
+        sum += -g.cn[k][0] * face_integral(Xi[a], Xi[bb], Xi[c], g.area[k], msub, kind, prm);
       }
       b[(size_t)i + (size_t)n_tet * r] = sum;
     }

@@ -1,0 +1,210 @@
+"""GB300 space-time Galerkin BEM for the retarded single layer of the 3D wave
+equation (Poelz & Schanz, "On the space-time discretization of variational
+retarded potential boundary integral equations").
+
+Thin Python layer over the C ABI of libstbem.so (include/stbem.h). The CUDA
+library does all computation; PyTorch is used only for device memory and
+streams where the caller passes device tensors. Importing this package does
+not load the library; the first object created does, and fails loudly when
+the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import BemError, DATA_PULSE, DATA_SIN2_UNIFORM
+
+__all__ = ["Context", "Mesh", "Operator", "inner_potentials", "BemError", "DATA_PULSE", "DATA_SIN2_UNIFORM"]
+
+
+class Context:
+    """bem_context: binds one CUDA device and owns the library's stream."""
+
+    def __init__(self, device: int = 0):
+        self._L = _lib.load()
+        h = ctypes.c_void_p()
+        _lib.check(self._L.bem_context_create(int(device), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.bem_context_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def version():
+        return _lib.load().bem_version().decode()
+
+
+class Mesh:
+    """bem_mesh: a space-time tetrahedral mesh of Gamma x [0, T]."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.h = handle
+        n = np.zeros(3, dtype=np.int64)
+        _lib.check(ctx._L.bem_mesh_info(self.h, _lib.lptr(n[0:1]), _lib.lptr(n[1:2]), _lib.lptr(n[2:3])))
+        self.n_tet, self.n_columns, self.n_surfaces = (int(v) for v in n)
+
+    @classmethod
+    def from_tets(cls, ctx, sv_xyz, stv_sv, stv_t, tets):
+        sv_xyz = np.ascontiguousarray(sv_xyz, dtype=np.float64)
+        stv_sv = np.ascontiguousarray(stv_sv, dtype=np.int32)
+        stv_t = np.ascontiguousarray(stv_t, dtype=np.float64)
+        tets = np.ascontiguousarray(tets, dtype=np.int32)
+        h = ctypes.c_void_p()
+        _lib.check(ctx._L.bem_mesh_create(ctx.h, sv_xyz.shape[0], _lib.dptr(sv_xyz), stv_sv.shape[0],
+                                          _lib.iptr(stv_sv), _lib.dptr(stv_t), tets.shape[0], _lib.iptr(tets),
+                                          ctypes.byref(h)))
+        return cls(ctx, h)
+
+    @classmethod
+    def from_prisms(cls, ctx, sv_xyz, tri, time_nodes):
+        sv_xyz = np.ascontiguousarray(sv_xyz, dtype=np.float64)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        tn = np.ascontiguousarray(time_nodes, dtype=np.float64)
+        h = ctypes.c_void_p()
+        _lib.check(ctx._L.bem_mesh_create_prisms(ctx.h, sv_xyz.shape[0], _lib.dptr(sv_xyz), tri.shape[0],
+                                                 _lib.iptr(tri), tn.shape[1] - 1, _lib.dptr(tn), ctypes.byref(h)))
+        return cls(ctx, h)
+
+    @classmethod
+    def from_spacetime(cls, ctx, m):
+        """From a paper_2103_16841_gb300.inputs.SpaceTimeMesh."""
+        return cls.from_tets(ctx, m.svert, m.stv_sv, m.stv_t, m.tets)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx._L.bem_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Operator:
+    """bem_operator: the assembled energetic single-layer Galerkin matrix."""
+
+    def __init__(self, ctx: Context, mesh: Mesh, precision: str = "fp64", m_q: int = 3, n_theta: int = 0,
+                 store_fp32: bool = True):
+        self.ctx, self.mesh = ctx, mesh
+        o = _lib.OpOpts(_lib.PREC[precision], int(m_q), int(n_theta), int(bool(store_fp32)))
+        h = ctypes.c_void_p()
+        _lib.check(ctx._L.bem_operator_create(ctx.h, mesh.h, ctypes.byref(o), ctypes.byref(h)))
+        self.h = h
+        self.n = mesh.n_tet
+
+    def stats(self):
+        a = np.zeros(3, dtype=np.int64)
+        ms = np.zeros(1)
+        _lib.check(self.ctx._L.bem_operator_stats(self.h, _lib.lptr(a[0:1]), _lib.lptr(a[1:2]), _lib.lptr(a[2:3]),
+                                                  _lib.dptr(ms)))
+        return {"nnz": int(a[0]), "stored": int(a[1]), "blocks": int(a[2]), "assemble_ms": float(ms[0])}
+
+    def timings(self):
+        ms = np.zeros(4)
+        _lib.check(self.ctx._L.bem_operator_timings(self.h, _lib.dptr(ms)))
+        return {"outer_points_ms": ms[0], "pattern_ms": ms[1], "offsets_ms": ms[2], "quadrature_ms": ms[3]}
+
+    def reassemble(self, stream=None):
+        _lib.check(self.ctx._L.bem_operator_reassemble(self.h, _stream_ptr(stream)))
+
+    def export_pattern(self):
+        nnz = self.stats()["nnz"]
+        rowptr = np.zeros(self.n + 1, dtype=np.int64)
+        cols = np.zeros(max(nnz, 1), dtype=np.int32)
+        _lib.check(self.ctx._L.bem_operator_export_pattern(self.h, _lib.lptr(rowptr), _lib.iptr(cols)))
+        return rowptr, cols[:nnz]
+
+    def export_dense(self):
+        A = np.zeros((self.n, self.n))
+        _lib.check(self.ctx._L.bem_operator_export_dense(self.h, _lib.dptr(A)))
+        return A
+
+    def entries(self, ij):
+        ij = np.ascontiguousarray(np.asarray(ij, dtype=np.int32).reshape(-1, 2))
+        out = np.zeros(ij.shape[0])
+        _lib.check(self.ctx._L.bem_operator_entries(self.h, ij.shape[0], _lib.iptr(ij), _lib.dptr(out)))
+        return out
+
+    def rhs(self, kind, params=None):
+        if params is not None:
+            params = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 5)
+            nrhs = params.shape[0]
+            pp = _lib.dptr(params)
+        else:
+            nrhs = 1
+            pp = ctypes.POINTER(ctypes.c_double)()
+        b = np.zeros(nrhs * self.n)
+        _lib.check(self.ctx._L.bem_rhs(self.h, int(kind), nrhs, pp, _lib.dptr(b)))
+        return b.reshape(nrhs, self.n).T.copy()
+
+    def matvec(self, x, y=None, stream=None):
+        """y = A x for torch CUDA float64 tensors of shape [n] or [nrhs, n]."""
+        import torch
+        if not (x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+            raise ValueError("x must be a contiguous CUDA float64 tensor")
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        if y is None:
+            y = torch.empty_like(x)
+        _lib.check(self.ctx._L.bem_matvec(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                          nrhs, _stream_ptr(stream)))
+        return y
+
+    def solve(self, b, tol=1e-8, restart=50, maxit=2000, inner="fp64", max_refine=10, allow_unconverged=False):
+        """Host arrays b [n] or [n, nrhs]; returns (w, infos)."""
+        b = np.asarray(b, dtype=np.float64)
+        vec = b.ndim == 1
+        B = np.ascontiguousarray((b[:, None] if vec else b).T)
+        nrhs = B.shape[0]
+        W = np.zeros_like(B)
+        o = _lib.SolveOpts(float(tol), int(restart), int(maxit), _lib.DTYPE[inner], int(max_refine))
+        info = (_lib.SolveInfo * nrhs)()
+        st = self.ctx._L.bem_solve(self.h, _lib.dptr(B), _lib.dptr(W), nrhs, ctypes.byref(o), info)
+        _lib.check(st, allow=(4,) if allow_unconverged else ())
+        infos = [{"iterations": i.iterations, "refinements": i.refinements, "converged": bool(i.converged),
+                  "rel_residual": i.rel_residual, "solve_ms": i.solve_ms} for i in info]
+        w = W.T.copy()
+        return (w[:, 0] if vec else w), infos
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx._L.bem_operator_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def inner_potentials(ctx: Context, x4, tets, tet_sv, precision="fp64", n_theta=0):
+    """V 1_sigma(x) for arrays of apexes x4 [n,4] and panels tets [n,4,4] (t,x,y,z)."""
+    x4 = np.ascontiguousarray(x4, dtype=np.float64).reshape(-1, 4)
+    tets = np.ascontiguousarray(tets, dtype=np.float64).reshape(-1, 4, 4)
+    sv = np.ascontiguousarray(tet_sv, dtype=np.int32).reshape(-1, 4)
+    out = np.zeros(x4.shape[0])
+    _lib.check(ctx._L.bem_inner_potentials(ctx.h, x4.shape[0], _lib.dptr(x4), _lib.dptr(tets), _lib.iptr(sv),
+                                           _lib.PREC[precision], int(n_theta), _lib.dptr(out)))
+    return out
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))

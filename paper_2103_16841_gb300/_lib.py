@@ -1,0 +1,127 @@
+"""ctypes binding of libstbem.so (the C ABI declared in include/stbem.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library. The library is loaded from the package's build directory; if it is
+missing, loading fails loudly (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+BEM_OK = 0
+STATUS = {0: "BEM_OK", 1: "BEM_ERR_INVALID_ARG", 2: "BEM_ERR_OUT_OF_MEMORY", 3: "BEM_ERR_CUDA",
+          4: "BEM_ERR_NOT_CONVERGED", 5: "BEM_ERR_DEVICE_TIMEOUT", 6: "BEM_ERR_UNSUPPORTED",
+          7: "BEM_ERR_BAD_MESH", 8: "BEM_ERR_INTERNAL"}
+PREC = {"fp64": 0, "mixed": 1}
+DTYPE = {"fp64": 0, "fp32": 1}
+DATA_SIN2_UNIFORM = 0
+DATA_PULSE = 1
+
+# every symbol include/stbem.h declares
+EXPORTS = [
+    "bem_context_create", "bem_context_destroy", "bem_last_error", "bem_version",
+    "bem_mesh_create", "bem_mesh_create_prisms", "bem_mesh_info", "bem_mesh_destroy",
+    "bem_operator_create", "bem_operator_stats", "bem_operator_timings", "bem_operator_reassemble", "bem_operator_export_pattern",
+    "bem_operator_export_dense", "bem_operator_entries", "bem_operator_destroy",
+    "bem_rhs", "bem_matvec", "bem_solve", "bem_solve_device", "bem_inner_potentials",
+]
+
+
+class BemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class OpOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("m_q", ctypes.c_int32), ("n_theta", ctypes.c_int32),
+                ("store_fp32", ctypes.c_int32)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
+                ("inner_dtype", ctypes.c_int32), ("max_refine", ctypes.c_int32)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+
+_lib = None
+VP = ctypes.c_void_p
+D = ctypes.POINTER(ctypes.c_double)
+I32 = ctypes.POINTER(ctypes.c_int32)
+I64 = ctypes.POINTER(ctypes.c_int64)
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+        _build.build()
+    L = ctypes.CDLL(path)
+    L.bem_last_error.restype = ctypes.c_char_p
+    L.bem_version.restype = ctypes.c_char_p
+    L.bem_context_create.argtypes = [ctypes.c_int, ctypes.POINTER(VP)]
+    L.bem_context_destroy.argtypes = [VP]
+    L.bem_context_destroy.restype = None
+    L.bem_mesh_create.argtypes = [VP, ctypes.c_int64, D, ctypes.c_int64, I32, D, ctypes.c_int64, I32,
+                                  ctypes.POINTER(VP)]
+    L.bem_mesh_create_prisms.argtypes = [VP, ctypes.c_int64, D, ctypes.c_int64, I32, ctypes.c_int32, D,
+                                         ctypes.POINTER(VP)]
+    L.bem_mesh_info.argtypes = [VP, I64, I64, I64]
+    L.bem_mesh_destroy.argtypes = [VP]
+    L.bem_mesh_destroy.restype = None
+    L.bem_operator_create.argtypes = [VP, VP, ctypes.POINTER(OpOpts), ctypes.POINTER(VP)]
+    L.bem_operator_stats.argtypes = [VP, I64, I64, I64, D]
+    L.bem_operator_reassemble.argtypes = [VP, VP]
+    L.bem_operator_timings.argtypes = [VP, D]
+    L.bem_operator_export_pattern.argtypes = [VP, I64, I32]
+    L.bem_operator_export_dense.argtypes = [VP, D]
+    L.bem_operator_entries.argtypes = [VP, ctypes.c_int64, I32, D]
+    L.bem_operator_destroy.argtypes = [VP]
+    L.bem_operator_destroy.restype = None
+    L.bem_rhs.argtypes = [VP, ctypes.c_int32, ctypes.c_int32, D, D]
+    L.bem_matvec.argtypes = [VP, VP, VP, ctypes.c_int32, VP]
+    L.bem_solve.argtypes = [VP, D, D, ctypes.c_int32, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]
+    L.bem_solve_device.argtypes = [VP, VP, VP, ctypes.c_int32, ctypes.POINTER(SolveOpts),
+                                   ctypes.POINTER(SolveInfo), VP]
+    L.bem_inner_potentials.argtypes = [VP, ctypes.c_int64, D, D, I32, ctypes.c_int32, ctypes.c_int32, D]
+    for name in EXPORTS:
+        if name not in ("bem_context_destroy", "bem_mesh_destroy", "bem_operator_destroy", "bem_last_error",
+                        "bem_version"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def check(status, allow=()):
+    if status != BEM_OK and status not in allow:
+        raise BemError(status, load().bem_last_error().decode())
+    return status
+
+
+def dptr(a: np.ndarray):
+    return a.ctypes.data_as(D)
+
+
+def iptr(a: np.ndarray):
+    return a.ctypes.data_as(I32)
+
+
+def lptr(a: np.ndarray):
+    return a.ctypes.data_as(I64)

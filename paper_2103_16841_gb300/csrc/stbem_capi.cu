@@ -1,0 +1,671 @@
+// C ABI of the library: mesh topology (host), operator lifecycle, data
+// movement between the caller's panel numbering and the internal order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "stbem_internal.h"
+
+namespace stbem {
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+int quad_grid(const bem_operator* op);
+}  // namespace stbem
+
+using namespace stbem;
+
+namespace {
+
+template <typename T>
+bem_status dalloc(T** p, size_t n) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? BEM_ERR_OUT_OF_MEMORY : BEM_ERR_CUDA;
+  }
+  return BEM_OK;
+}
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  ~DevBuf() { if (p) cudaFree(p); }
+  bem_status alloc(size_t n) { return dalloc(&p, n); }
+};
+
+#define TRY(x)                        \
+  do {                                \
+    bem_status s_ = (x);              \
+    if (s_ != BEM_OK) return s_;      \
+  } while (0)
+
+bool g_tables_ready = false;
+
+cudaStream_t pick(const bem_context* ctx, void* stream) {
+  return stream ? (cudaStream_t)stream : ctx->stream;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bem_last_error(void) { return g_last_error.c_str(); }
+const char* bem_version(void) { return "stbem-gb300 0.1 (sm_103a)"; }
+
+bem_status bem_context_create(int device, bem_context** out) {
+  if (!out) { set_error("null out"); return BEM_ERR_INVALID_ARG; }
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    set_error(std::string("no CUDA device: ") + cudaGetErrorString(e));
+    return BEM_ERR_CUDA;
+  }
+  if (device < 0 || device >= n) { set_error("device index out of range"); return BEM_ERR_INVALID_ARG; }
+  STBEM_CUDA(cudaSetDevice(device));
+  std::unique_ptr<bem_context> ctx(new bem_context());
+  ctx->device = device;
+  STBEM_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  ctx->sm_count = sms;
+  if (!g_tables_ready) {
+    TRY(upload_gauss_tables());
+    g_tables_ready = true;
+  }
+  *out = ctx.release();
+  return BEM_OK;
+}
+
+void bem_context_destroy(bem_context* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+bem_status bem_mesh_create(bem_context* ctx, int64_t n_sv, const double* sv_xyz, int64_t n_stv, const int32_t* stv_sv,
+                           const double* stv_t, int64_t n_tet, const int32_t* tets, bem_mesh** out) {
+  if (!ctx || !out || !sv_xyz || !stv_sv || !stv_t || !tets || n_sv <= 0 || n_stv <= 0 || n_tet <= 0) {
+    set_error("bem_mesh_create: invalid argument");
+    return BEM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  STBEM_CUDA(cudaSetDevice(ctx->device));
+  for (int64_t v = 0; v < n_stv; ++v)
+    if (stv_sv[v] < 0 || stv_sv[v] >= n_sv) { set_error("stv_sv out of range"); return BEM_ERR_BAD_MESH; }
+  struct TetH {
+    int col, dup;
+    int cs[3];      // corner spatial ids ascending
+    int lo_v[3], hi_v[3];  // space-time vertex at each corner for the lower / upper face
+    double tmin, tmax;
+    int user;
+  };
+  std::vector<TetH> T(n_tet);
+  std::map<std::array<int, 3>, int> colmap;
+  std::vector<std::array<int, 3>> col_corners;
+  double scale = 0.0;
+  for (int64_t v = 0; v < n_stv; ++v) scale = std::max(scale, std::fabs(stv_t[v]));
+  for (int64_t v = 0; v < 3 * n_sv; ++v) scale = std::max(scale, std::fabs(sv_xyz[v]));
+  for (int64_t i = 0; i < n_tet; ++i) {
+    const int32_t* tv = tets + 4 * i;
+    int sid[4];
+    for (int k = 0; k < 4; ++k) {
+      if (tv[k] < 0 || tv[k] >= n_stv) { set_error("tet vertex out of range"); return BEM_ERR_BAD_MESH; }
+      sid[k] = stv_sv[tv[k]];
+    }
+    std::array<int, 3> cs{};
+    int nc = 0;
+    for (int k = 0; k < 4; ++k) {
+      bool seen = false;
+      for (int q = 0; q < nc; ++q) seen |= cs[q] == sid[k];
+      if (!seen) {
+        if (nc == 3) { nc = 4; break; }
+        cs[nc++] = sid[k];
+      }
+    }
+    if (nc != 3) {
+      set_error("panel " + std::to_string(i) + " is not flat in Gamma_K x R (needs exactly 3 spatial vertices)");
+      return BEM_ERR_BAD_MESH;
+    }
+    std::sort(cs.begin(), cs.end());
+    TetH& h = T[i];
+    h.user = (int)i;
+    h.dup = -1;
+    for (int c = 0; c < 3; ++c) {
+      h.cs[c] = cs[c];
+      int vs[2], nv = 0;
+      for (int k = 0; k < 4; ++k)
+        if (sid[k] == cs[c]) vs[nv++] = tv[k];
+      if (nv == 1) { h.lo_v[c] = h.hi_v[c] = vs[0]; }
+      else {
+        if (stv_t[vs[0]] == stv_t[vs[1]]) {
+          set_error("panel " + std::to_string(i) + " has a vertical edge of zero length");
+          return BEM_ERR_BAD_MESH;
+        }
+        bool first_lo = stv_t[vs[0]] < stv_t[vs[1]];
+        h.lo_v[c] = first_lo ? vs[0] : vs[1];
+        h.hi_v[c] = first_lo ? vs[1] : vs[0];
+        h.dup = c;
+      }
+    }
+    // non-degenerate triangle
+    const double* a = sv_xyz + 3 * cs[0];
+    const double* b = sv_xyz + 3 * cs[1];
+    const double* cc = sv_xyz + 3 * cs[2];
+    double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, w[3] = {cc[0] - a[0], cc[1] - a[1], cc[2] - a[2]};
+    double nx = u[1] * w[2] - u[2] * w[1], ny = u[2] * w[0] - u[0] * w[2], nz = u[0] * w[1] - u[1] * w[0];
+    double l2 = std::max(u[0] * u[0] + u[1] * u[1] + u[2] * u[2], w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    if (!(std::sqrt(nx * nx + ny * ny + nz * nz) > 1e-12 * l2)) {
+      set_error("panel " + std::to_string(i) + " has a degenerate spatial triangle");
+      return BEM_ERR_BAD_MESH;
+    }
+    h.tmin = 1e300; h.tmax = -1e300;
+    for (int k = 0; k < 4; ++k) {
+      h.tmin = std::min(h.tmin, stv_t[tv[k]]);
+      h.tmax = std::max(h.tmax, stv_t[tv[k]]);
+    }
+    auto it = colmap.find(cs);
+    if (it == colmap.end()) {
+      it = colmap.emplace(cs, (int)col_corners.size()).first;
+      col_corners.push_back(cs);
+    }
+    h.col = it->second;
+  }
+  const int64_t n_col = (int64_t)col_corners.size();
+  // internal order: column, then time
+  std::vector<int32_t> perm(n_tet);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) {
+    const TetH &A = T[a], &B = T[b];
+    if (A.col != B.col) return A.col < B.col;
+    if (A.tmin != B.tmin) return A.tmin < B.tmin;
+    return A.tmax < B.tmax;
+  });
+  std::vector<int32_t> iperm(n_tet);
+  for (int64_t i = 0; i < n_tet; ++i) iperm[perm[i]] = (int32_t)i;
+  std::vector<int32_t> col_tet_begin(n_col + 1, 0);
+  for (int64_t i = 0; i < n_tet; ++i) col_tet_begin[T[perm[i]].col + 1]++;
+  for (int64_t c = 0; c < n_col; ++c) col_tet_begin[c + 1] += col_tet_begin[c];
+  // faces with nu_t != 0, numbered per column in order of first appearance
+  std::vector<std::map<std::array<int, 3>, int>> smap(n_col);
+  std::vector<std::vector<std::array<int, 3>>> scols(n_col);
+  std::vector<int> tlo(n_tet), thi(n_tet);
+  for (int64_t i = 0; i < n_tet; ++i) {
+    const TetH& h = T[perm[i]];
+    std::array<int, 3> klo{h.lo_v[0], h.lo_v[1], h.lo_v[2]}, khi{h.hi_v[0], h.hi_v[1], h.hi_v[2]};
+    for (int pass = 0; pass < 2; ++pass) {
+      auto& key = pass ? khi : klo;
+      auto it = smap[h.col].find(key);
+      if (it == smap[h.col].end()) {
+        it = smap[h.col].emplace(key, (int)scols[h.col].size()).first;
+        scols[h.col].push_back(key);
+      }
+      (pass ? thi : tlo)[i] = it->second;
+    }
+  }
+  std::vector<int32_t> col_surf_begin(n_col + 1, 0);
+  int max_tets = 0, max_surf = 0;
+  for (int64_t c = 0; c < n_col; ++c) {
+    col_surf_begin[c + 1] = col_surf_begin[c] + (int)scols[c].size();
+    max_tets = std::max(max_tets, col_tet_begin[c + 1] - col_tet_begin[c]);
+    max_surf = std::max(max_surf, (int)scols[c].size());
+  }
+  if (max_tets > MAX_COL_TETS || max_surf > MAX_COL_SURF) {
+    set_error("more than " + std::to_string(MAX_COL_TETS) + " panels over one spatial triangle");
+    return BEM_ERR_UNSUPPORTED;
+  }
+  const int64_t n_surf = col_surf_begin[n_col];
+  std::vector<int32_t> surf_col(n_surf);
+  std::vector<double> surf_p(3 * n_surf);
+  for (int64_t c = 0; c < n_col; ++c)
+    for (size_t s = 0; s < scols[c].size(); ++s) {
+      int64_t g = col_surf_begin[c] + s;
+      surf_col[g] = (int32_t)c;
+      for (int k = 0; k < 3; ++k) surf_p[3 * g + k] = stv_t[scols[c][s][k]];
+    }
+  std::vector<TetDev> td(n_tet);
+  std::vector<double> tvx(16 * n_tet);
+  for (int64_t i = 0; i < n_tet; ++i) {
+    const TetH& h = T[perm[i]];
+    TetDev& d = td[i];
+    d.col = h.col;
+    d.lo = col_surf_begin[h.col] + tlo[i];
+    d.hi = col_surf_begin[h.col] + thi[i];
+    d.dup = h.dup;
+    d.tmin = h.tmin;
+    d.tmax = h.tmax;
+    bool first = i == col_tet_begin[h.col];
+    d.pmax = first ? h.tmax : std::max(td[i - 1].pmax, h.tmax);
+    for (int c = 0; c < 3; ++c) d.vt[c] = stv_t[h.lo_v[c]];
+    d.vt[3] = stv_t[h.hi_v[h.dup]];
+    for (int k = 0; k < 5; ++k) d.ball[k] = 0.0;
+    const int32_t* tv = tets + 4 * (int64_t)perm[i];
+    for (int k = 0; k < 4; ++k) {
+      tvx[16 * i + 4 * k] = stv_t[tv[k]];
+      for (int q = 0; q < 3; ++q) tvx[16 * i + 4 * k + 1 + q] = sv_xyz[3 * stv_sv[tv[k]] + q];
+    }
+  }
+  std::vector<int32_t> corner_sv(3 * n_col);
+  for (int64_t c = 0; c < n_col; ++c)
+    for (int k = 0; k < 3; ++k) corner_sv[3 * c + k] = col_corners[c][k];
+  std::unique_ptr<bem_mesh> m(new bem_mesh());
+  m->ctx = ctx;
+  m->n_tet = n_tet; m->n_col = n_col; m->n_surf = n_surf;
+  m->max_col_tets = max_tets; m->max_col_surf = max_surf;
+  m->perm = perm; m->iperm = iperm;
+  m->col_tet_begin = col_tet_begin; m->col_surf_begin = col_surf_begin;
+  m->coord_scale = std::max(scale, 1e-300);
+  cudaStream_t s = ctx->stream;
+  TRY(dalloc(&m->d_col, n_col));
+  TRY(dalloc(&m->d_col_tet_begin, n_col + 1));
+  TRY(dalloc(&m->d_col_surf_begin, n_col + 1));
+  TRY(dalloc(&m->d_surf, n_surf));
+  TRY(dalloc(&m->d_tet, n_tet));
+  TRY(dalloc(&m->d_perm, n_tet));
+  DevBuf<double> d_sv, d_tvx, d_sp;
+  DevBuf<int32_t> d_cs, d_scol;
+  TRY(d_sv.alloc(3 * n_sv));
+  TRY(d_tvx.alloc(16 * n_tet));
+  TRY(d_sp.alloc(3 * n_surf));
+  TRY(d_cs.alloc(3 * n_col));
+  TRY(d_scol.alloc(n_surf));
+  STBEM_CUDA(cudaMemcpyAsync(d_sv.p, sv_xyz, sizeof(double) * 3 * n_sv, cudaMemcpyHostToDevice, s));
+  STBEM_CUDA(cudaMemcpyAsync(d_tvx.p, tvx.data(), sizeof(double) * 16 * n_tet, cudaMemcpyHostToDevice, s));
+  STBEM_CUDA(cudaMemcpyAsync(d_sp.p, surf_p.data(), sizeof(double) * 3 * n_surf, cudaMemcpyHostToDevice, s));
+  STBEM_CUDA(cudaMemcpyAsync(d_cs.p, corner_sv.data(), sizeof(int32_t) * 3 * n_col, cudaMemcpyHostToDevice, s));
+  STBEM_CUDA(cudaMemcpyAsync(d_scol.p, surf_col.data(), sizeof(int32_t) * n_surf, cudaMemcpyHostToDevice, s));
+  STBEM_CUDA(cudaMemcpyAsync(m->d_tet, td.data(), sizeof(TetDev) * n_tet, cudaMemcpyHostToDevice, s));
+  STBEM_CUDA(cudaMemcpyAsync(m->d_col_tet_begin, col_tet_begin.data(), sizeof(int32_t) * (n_col + 1),
+                             cudaMemcpyHostToDevice, s));
+  STBEM_CUDA(cudaMemcpyAsync(m->d_col_surf_begin, col_surf_begin.data(), sizeof(int32_t) * (n_col + 1),
+                             cudaMemcpyHostToDevice, s));
+  STBEM_CUDA(cudaMemcpyAsync(m->d_perm, perm.data(), sizeof(int32_t) * n_tet, cudaMemcpyHostToDevice, s));
+  TRY(mesh_device_geometry(m.get(), d_sv.p, d_cs.p, d_tvx.p, d_scol.p, d_sp.p));
+  STBEM_CUDA(cudaStreamSynchronize(s));
+  *out = m.release();
+  return BEM_OK;
+}
+
+bem_status bem_mesh_create_prisms(bem_context* ctx, int64_t n_sv, const double* sv_xyz, int64_t n_tri,
+                                  const int32_t* tri, int32_t n_slabs, const double* time_nodes, bem_mesh** out) {
+  if (!ctx || !sv_xyz || !tri || !time_nodes || !out || n_sv <= 0 || n_tri <= 0 || n_slabs <= 0) {
+    set_error("bem_mesh_create_prisms: invalid argument");
+    return BEM_ERR_INVALID_ARG;
+  }
+  const int64_t ns1 = n_slabs + 1;
+  std::vector<int32_t> stv_sv(n_sv * ns1);
+  std::vector<double> stv_t(n_sv * ns1);
+  for (int64_t v = 0; v < n_sv; ++v)
+    for (int64_t n = 0; n < ns1; ++n) {
+      stv_sv[v * ns1 + n] = (int32_t)v;
+      stv_t[v * ns1 + n] = time_nodes[v * ns1 + n];
+      if (n > 0 && !(time_nodes[v * ns1 + n] > time_nodes[v * ns1 + n - 1])) {
+        set_error("time nodes must increase");
+        return BEM_ERR_BAD_MESH;
+      }
+    }
+  std::vector<int32_t> tets(12 * n_tri * n_slabs);
+  for (int64_t k = 0; k < n_tri; ++k) {
+    int v[3] = {tri[3 * k], tri[3 * k + 1], tri[3 * k + 2]};
+    std::sort(v, v + 3);
+    for (int64_t n = 0; n < n_slabs; ++n) {
+      int32_t A0 = (int32_t)(v[0] * ns1 + n), B0 = (int32_t)(v[1] * ns1 + n), C0 = (int32_t)(v[2] * ns1 + n);
+      int32_t* t = tets.data() + 12 * (k * n_slabs + n);
+      int32_t loc[12] = {A0, B0, C0, A0 + 1, B0, C0, A0 + 1, B0 + 1, C0, A0 + 1, B0 + 1, C0 + 1};
+      std::memcpy(t, loc, sizeof(loc));
+    }
+  }
+  return bem_mesh_create(ctx, n_sv, sv_xyz, n_sv * ns1, stv_sv.data(), stv_t.data(), 3 * n_tri * n_slabs,
+                         tets.data(), out);
+}
+
+bem_status bem_mesh_info(const bem_mesh* m, int64_t* n_tet, int64_t* n_columns, int64_t* n_surfaces) {
+  if (!m) { set_error("null mesh"); return BEM_ERR_INVALID_ARG; }
+  if (n_tet) *n_tet = m->n_tet;
+  if (n_columns) *n_columns = m->n_col;
+  if (n_surfaces) *n_surfaces = m->n_surf;
+  return BEM_OK;
+}
+
+void bem_mesh_destroy(bem_mesh* m) {
+  if (!m) return;
+  cudaFree(m->d_col); cudaFree(m->d_col_tet_begin); cudaFree(m->d_col_surf_begin);
+  cudaFree(m->d_surf); cudaFree(m->d_tet); cudaFree(m->d_perm);
+  delete m;
+}
+
+}  // extern "C"
+
+namespace {
+
+bem_status assemble(bem_operator* op, cudaStream_t s, bool first) {
+  const bem_mesh* m = op->mesh;
+  const int64_t nb = m->n_col * m->n_col;
+  cudaEvent_t e0, e1, ea, eb, ec;
+  STBEM_CUDA(cudaEventCreate(&e0));
+  STBEM_CUDA(cudaEventCreate(&e1));
+  STBEM_CUDA(cudaEventCreate(&ea));
+  STBEM_CUDA(cudaEventCreate(&eb));
+  STBEM_CUDA(cudaEventCreate(&ec));
+  STBEM_CUDA(cudaEventRecord(e0, s));
+  TRY(op_outer_points(op, s));
+  STBEM_CUDA(cudaEventRecord(ea, s));
+  TRY(op_pattern(op, s));
+  STBEM_CUDA(cudaEventRecord(eb, s));
+  std::vector<int32_t> bw(nb);
+  std::vector<int64_t> bnnz(nb);
+  STBEM_CUDA(cudaMemcpyAsync(bw.data(), op->d_bw, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, s));
+  STBEM_CUDA(cudaMemcpyAsync(bnnz.data(), op->d_bnnz, sizeof(int64_t) * nb, cudaMemcpyDeviceToHost, s));
+  STBEM_CUDA(cudaStreamSynchronize(s));
+  std::vector<int64_t> boff(nb), rsoff(nb);
+  int64_t vo = 0, ro = 0, nnz = 0, nblk = 0;
+  for (int64_t I = 0; I < m->n_col; ++I) {
+    int R = m->col_tet_begin[I + 1] - m->col_tet_begin[I];
+    for (int64_t J = 0; J < m->n_col; ++J) {
+      int64_t b = I * m->n_col + J;
+      boff[b] = vo;
+      rsoff[b] = ro;
+      if (bw[b] > 0) {
+        vo += (int64_t)R * bw[b];
+        ro += R;
+        ++nblk;
+      }
+      nnz += bnnz[b];
+    }
+  }
+  if (first) {
+    op->nstored = vo; op->nrows_stored = ro; op->nnz = nnz; op->nblocks = nblk;
+    TRY(dalloc(&op->d_val, (size_t)vo));
+    if (op->opts.store_fp32) TRY(dalloc(&op->d_val32, (size_t)vo));
+    TRY(dalloc(&op->d_rs, (size_t)ro));
+    int grid = quad_grid(op);
+    op->tmp_len = std::max<int64_t>((int64_t)grid * m->max_col_surf * m->max_col_tets, 2 * m->n_tet * 8);
+    TRY(dalloc(&op->d_tmp, (size_t)op->tmp_len));
+  } else if (vo != op->nstored || nnz != op->nnz) {
+    set_error("reassembly changed the sparsity structure");
+    return BEM_ERR_INTERNAL;
+  }
+  STBEM_CUDA(cudaMemcpyAsync(op->d_boff, boff.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, s));
+  STBEM_CUDA(cudaMemcpyAsync(op->d_rsoff, rsoff.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, s));
+  STBEM_CUDA(cudaEventRecord(ec, s));
+  TRY(op_quadrature(op, s));
+  STBEM_CUDA(cudaEventRecord(e1, s));
+  STBEM_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventElapsedTime(&m0, e0, ea);
+  cudaEventElapsedTime(&m1, ea, eb);
+  cudaEventElapsedTime(&m2, eb, ec);
+  cudaEventElapsedTime(&m3, ec, e1);
+  op->assemble_ms = ms;
+  op->phase_ms[0] = m0; op->phase_ms[1] = m1; op->phase_ms[2] = m2; op->phase_ms[3] = m3;
+  for (cudaEvent_t e : {e0, e1, ea, eb, ec}) cudaEventDestroy(e);
+  STBEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bem_status bem_operator_create(bem_context* ctx, const bem_mesh* mesh, const bem_op_opts* opts, bem_operator** out) {
+  if (!ctx || !mesh || !out) { set_error("bem_operator_create: invalid argument"); return BEM_ERR_INVALID_ARG; }
+  *out = nullptr;
+  bem_op_opts o{};
+  o.precision = BEM_PREC_FP64; o.m_q = 3; o.n_theta = 0; o.store_fp32 = 1;
+  if (opts) o = *opts;
+  if (o.precision != BEM_PREC_FP64 && o.precision != BEM_PREC_MIXED) {
+    set_error("unknown precision"); return BEM_ERR_INVALID_ARG;
+  }
+  if (o.m_q < 1 || o.m_q > 4) { set_error("m_q must be in 1..4"); return BEM_ERR_UNSUPPORTED; }
+  if (o.n_theta != 0 && (o.n_theta < 4 || o.n_theta > MAX_NTHETA)) {
+    set_error("n_theta must be 0 or in 4..32");
+    return BEM_ERR_INVALID_ARG;
+  }
+  STBEM_CUDA(cudaSetDevice(ctx->device));
+  std::unique_ptr<bem_operator> op(new bem_operator());
+  op->ctx = ctx; op->mesh = mesh; op->opts = o;
+  op->mq = o.m_q; op->nq = o.m_q * o.m_q; op->n_theta = o.n_theta;
+  const int64_t nb = mesh->n_col * mesh->n_col;
+  TRY(dalloc(&op->d_pts, (size_t)mesh->n_surf * op->nq * 4));
+  TRY(dalloc(&op->d_pts_trange, (size_t)mesh->n_surf * 2));
+  TRY(dalloc(&op->d_bw, (size_t)nb));
+  TRY(dalloc(&op->d_bnnz, (size_t)nb));
+  TRY(dalloc(&op->d_boff, (size_t)nb));
+  TRY(dalloc(&op->d_rsoff, (size_t)nb));
+  TRY(dalloc(&op->d_counter, 4));
+  bem_status st = assemble(op.get(), ctx->stream, true);
+  if (st != BEM_OK) { bem_operator_destroy(op.release()); return st; }
+  *out = op.release();
+  return BEM_OK;
+}
+
+bem_status bem_operator_timings(const bem_operator* op, double* ms) {
+  if (!op || !ms) { set_error("invalid argument"); return BEM_ERR_INVALID_ARG; }
+  for (int k = 0; k < 4; ++k) ms[k] = op->phase_ms[k];
+  return BEM_OK;
+}
+
+bem_status bem_operator_reassemble(bem_operator* op, void* stream) {
+  if (!op) { set_error("null operator"); return BEM_ERR_INVALID_ARG; }
+  return assemble(op, pick(op->ctx, stream), false);
+}
+
+bem_status bem_operator_stats(const bem_operator* op, int64_t* nnz, int64_t* stored, int64_t* nblocks, double* ms) {
+  if (!op) { set_error("null operator"); return BEM_ERR_INVALID_ARG; }
+  if (nnz) *nnz = op->nnz;
+  if (stored) *stored = op->nstored;
+  if (nblocks) *nblocks = op->nblocks;
+  if (ms) *ms = op->assemble_ms;
+  return BEM_OK;
+}
+
+void bem_operator_destroy(bem_operator* op) {
+  if (!op) return;
+  cudaFree(op->d_pts); cudaFree(op->d_pts_trange); cudaFree(op->d_bw); cudaFree(op->d_bnnz);
+  cudaFree(op->d_boff); cudaFree(op->d_rsoff); cudaFree(op->d_rs); cudaFree(op->d_val);
+  cudaFree(op->d_val32); cudaFree(op->d_tmp); cudaFree(op->d_counter);
+  delete op;
+}
+
+bem_status bem_operator_export_pattern(const bem_operator* op, int64_t* rowptr, int32_t* cols) {
+  if (!op || !rowptr || !cols) { set_error("invalid argument"); return BEM_ERR_INVALID_ARG; }
+  const bem_mesh* m = op->mesh;
+  cudaStream_t s = op->ctx->stream;
+  const int64_t n = m->n_tet;
+  DevBuf<int64_t> cnt, rp;
+  DevBuf<int32_t> cl;
+  TRY(cnt.alloc(n)); TRY(rp.alloc(n + 1)); TRY(cl.alloc(std::max<int64_t>(op->nnz, 1)));
+  STBEM_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int64_t) * n, s));
+  TRY(op_pattern_csr(op, cnt.p, rp.p, cl.p, false, s));
+  std::vector<int64_t> hc(n), hp(n + 1, 0);
+  STBEM_CUDA(cudaMemcpyAsync(hc.data(), cnt.p, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s));
+  STBEM_CUDA(cudaStreamSynchronize(s));
+  for (int64_t i = 0; i < n; ++i) hp[i + 1] = hp[i] + hc[i];
+  if (hp[n] != op->nnz) { set_error("pattern count mismatch"); return BEM_ERR_INTERNAL; }
+  STBEM_CUDA(cudaMemcpyAsync(rp.p, hp.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
+  STBEM_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int64_t) * n, s));
+  TRY(op_pattern_csr(op, cnt.p, rp.p, cl.p, true, s));
+  std::vector<int32_t> hcl(std::max<int64_t>(op->nnz, 1));
+  STBEM_CUDA(cudaMemcpyAsync(hcl.data(), cl.p, sizeof(int32_t) * op->nnz, cudaMemcpyDeviceToHost, s));
+  STBEM_CUDA(cudaStreamSynchronize(s));
+  // caller numbering: row p = perm[i], columns perm[j], sorted
+  std::vector<int64_t> ucount(n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) ucount[m->perm[i] + 1] = hc[i];
+  for (int64_t i = 0; i < n; ++i) ucount[i + 1] += ucount[i];
+  for (int64_t i = 0; i <= n; ++i) rowptr[i] = ucount[i];
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t dst = rowptr[m->perm[i]];
+    for (int64_t k = hp[i]; k < hp[i + 1]; ++k) cols[dst + (k - hp[i])] = m->perm[hcl[k]];
+    std::sort(cols + dst, cols + dst + hc[i]);
+  }
+  return BEM_OK;
+}
+
+bem_status bem_operator_export_dense(const bem_operator* op, double* A) {
+  if (!op || !A) { set_error("invalid argument"); return BEM_ERR_INVALID_ARG; }
+  const bem_mesh* m = op->mesh;
+  const int64_t n = m->n_tet, nb = m->n_col * m->n_col;
+  if (n > 20000) { set_error("export_dense: mesh too large"); return BEM_ERR_UNSUPPORTED; }
+  cudaStream_t s = op->ctx->stream;
+  std::vector<int32_t> bw(nb), rs(std::max<int64_t>(op->nrows_stored, 1));
+  std::vector<int64_t> boff(nb), rsoff(nb);
+  std::vector<double> val(std::max<int64_t>(op->nstored, 1));
+  STBEM_CUDA(cudaMemcpyAsync(bw.data(), op->d_bw, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, s));
+  STBEM_CUDA(cudaMemcpyAsync(boff.data(), op->d_boff, sizeof(int64_t) * nb, cudaMemcpyDeviceToHost, s));
+  STBEM_CUDA(cudaMemcpyAsync(rsoff.data(), op->d_rsoff, sizeof(int64_t) * nb, cudaMemcpyDeviceToHost, s));
+  STBEM_CUDA(cudaMemcpyAsync(rs.data(), op->d_rs, sizeof(int32_t) * op->nrows_stored, cudaMemcpyDeviceToHost, s));
+  STBEM_CUDA(cudaMemcpyAsync(val.data(), op->d_val, sizeof(double) * op->nstored, cudaMemcpyDeviceToHost, s));
+  STBEM_CUDA(cudaStreamSynchronize(s));
+  std::memset(A, 0, sizeof(double) * n * n);
+  for (int64_t I = 0; I < m->n_col; ++I) {
+    int t0 = m->col_tet_begin[I], R = m->col_tet_begin[I + 1] - t0;
+    for (int64_t J = 0; J < m->n_col; ++J) {
+      int64_t b = I * m->n_col + J;
+      if (!bw[b]) continue;
+      int jend = m->col_tet_begin[J + 1];
+      for (int r = 0; r < R; ++r) {
+        int st = rs[rsoff[b] + r];
+        for (int w = 0; w < bw[b]; ++w) {
+          int j = st + w;
+          if (j >= jend) break;
+          A[(int64_t)m->perm[t0 + r] * n + m->perm[j]] = val[boff[b] + (int64_t)w * R + r];
+        }
+      }
+    }
+  }
+  return BEM_OK;
+}
+
+bem_status bem_operator_entries(const bem_operator* op, int64_t n, const int32_t* ij, double* out) {
+  if (!op || (n > 0 && (!ij || !out)) || n < 0) { set_error("invalid argument"); return BEM_ERR_INVALID_ARG; }
+  if (n == 0) return BEM_OK;
+  const bem_mesh* m = op->mesh;
+  std::vector<int32_t> in(2 * n);
+  for (int64_t k = 0; k < 2 * n; ++k) {
+    if (ij[k] < 0 || ij[k] >= m->n_tet) { set_error("entry index out of range"); return BEM_ERR_INVALID_ARG; }
+    in[k] = m->iperm[ij[k]];
+  }
+  cudaStream_t s = op->ctx->stream;
+  DevBuf<int32_t> dij;
+  DevBuf<double> dout;
+  TRY(dij.alloc(2 * n)); TRY(dout.alloc(n));
+  STBEM_CUDA(cudaMemcpyAsync(dij.p, in.data(), sizeof(int32_t) * 2 * n, cudaMemcpyHostToDevice, s));
+  TRY(op_entries(op, n, dij.p, dout.p, s));
+  STBEM_CUDA(cudaMemcpyAsync(out, dout.p, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  STBEM_CUDA(cudaStreamSynchronize(s));
+  return BEM_OK;
+}
+
+bem_status bem_rhs(const bem_operator* op, int32_t kind, int32_t nrhs, const double* params, double* b) {
+  if (!op || !b || nrhs <= 0 || (kind != BEM_DATA_SIN2_UNIFORM && kind != BEM_DATA_PULSE) ||
+      (kind == BEM_DATA_PULSE && !params)) {
+    set_error("bem_rhs: invalid argument");
+    return BEM_ERR_INVALID_ARG;
+  }
+  const bem_mesh* m = op->mesh;
+  cudaStream_t s = op->ctx->stream;
+  const int64_t nn = m->n_tet * nrhs;
+  DevBuf<double> dp, db, du;
+  TRY(db.alloc(nn)); TRY(du.alloc(nn));
+  if (params) {
+    TRY(dp.alloc(5 * nrhs));
+    STBEM_CUDA(cudaMemcpyAsync(dp.p, params, sizeof(double) * 5 * nrhs, cudaMemcpyHostToDevice, s));
+  }
+  TRY(op_rhs(op, kind, nrhs, dp.p, db.p, s));
+  TRY(permute(m->d_perm, db.p, du.p, m->n_tet, nrhs, false, s));
+  STBEM_CUDA(cudaMemcpyAsync(b, du.p, sizeof(double) * nn, cudaMemcpyDeviceToHost, s));
+  STBEM_CUDA(cudaStreamSynchronize(s));
+  return BEM_OK;
+}
+
+bem_status bem_matvec(const bem_operator* op, const double* x_dev, double* y_dev, int32_t nrhs, void* stream) {
+  if (!op || !x_dev || !y_dev || nrhs <= 0) { set_error("bem_matvec: invalid argument"); return BEM_ERR_INVALID_ARG; }
+  const bem_mesh* m = op->mesh;
+  cudaStream_t s = pick(op->ctx, stream);
+  const int64_t nn = m->n_tet * nrhs;
+  DevBuf<double> xi, yi;
+  TRY(xi.alloc(nn)); TRY(yi.alloc(nn));
+  TRY(permute(m->d_perm, x_dev, xi.p, m->n_tet, nrhs, true, s));
+  TRY(op_matvec(op, xi.p, yi.p, nrhs, false, s));
+  TRY(permute(m->d_perm, yi.p, y_dev, m->n_tet, nrhs, false, s));
+  STBEM_CUDA(cudaStreamSynchronize(s));
+  return BEM_OK;
+}
+
+bem_status bem_solve_device(bem_operator* op, const double* b_dev, double* w_dev, int32_t nrhs,
+                            const bem_solve_opts* opts, bem_solve_info* info, void* stream) {
+  if (!op || !b_dev || !w_dev || nrhs <= 0) { set_error("bem_solve: invalid argument"); return BEM_ERR_INVALID_ARG; }
+  bem_solve_opts o{1e-8, 50, 2000, BEM_DTYPE_FP64, 10};
+  if (opts) o = *opts;
+  if (o.restart < 1 || o.restart > 200 || o.maxit < 1 || !(o.tol > 0)) {
+    set_error("bem_solve: bad options");
+    return BEM_ERR_INVALID_ARG;
+  }
+  if (o.inner_dtype == BEM_DTYPE_FP32 && !op->d_val32) {
+    set_error("FP32 inner solves need store_fp32 = 1");
+    return BEM_ERR_INVALID_ARG;
+  }
+  const bem_mesh* m = op->mesh;
+  cudaStream_t s = pick(op->ctx, stream);
+  const int64_t nn = m->n_tet * nrhs;
+  DevBuf<double> bi, xi;
+  TRY(bi.alloc(nn)); TRY(xi.alloc(nn));
+  TRY(permute(m->d_perm, b_dev, bi.p, m->n_tet, nrhs, true, s));
+  bem_status st = gmres_solve(op, bi.p, xi.p, nrhs, &o, info, s);
+  if (st != BEM_OK && st != BEM_ERR_NOT_CONVERGED) return st;
+  TRY(permute(m->d_perm, xi.p, w_dev, m->n_tet, nrhs, false, s));
+  STBEM_CUDA(cudaStreamSynchronize(s));
+  return st;
+}
+
+bem_status bem_solve(bem_operator* op, const double* b, double* w, int32_t nrhs, const bem_solve_opts* opts,
+                     bem_solve_info* info) {
+  if (!op || !b || !w || nrhs <= 0) { set_error("bem_solve: invalid argument"); return BEM_ERR_INVALID_ARG; }
+  const int64_t nn = op->mesh->n_tet * nrhs;
+  cudaStream_t s = op->ctx->stream;
+  DevBuf<double> db, dw;
+  TRY(db.alloc(nn)); TRY(dw.alloc(nn));
+  STBEM_CUDA(cudaMemcpyAsync(db.p, b, sizeof(double) * nn, cudaMemcpyHostToDevice, s));
+  bem_status st = bem_solve_device(op, db.p, dw.p, nrhs, opts, info, s);
+  if (st != BEM_OK && st != BEM_ERR_NOT_CONVERGED) return st;
+  STBEM_CUDA(cudaMemcpyAsync(w, dw.p, sizeof(double) * nn, cudaMemcpyDeviceToHost, s));
+  STBEM_CUDA(cudaStreamSynchronize(s));
+  return st;
+}
+
+bem_status bem_inner_potentials(bem_context* ctx, int64_t n, const double* x4, const double* tets,
+                                const int32_t* tet_sv, int32_t precision, int32_t n_theta, double* out) {
+  if (!ctx || n < 0 || (n > 0 && (!x4 || !tets || !tet_sv || !out))) {
+    set_error("bem_inner_potentials: invalid argument");
+    return BEM_ERR_INVALID_ARG;
+  }
+  if (n_theta != 0 && (n_theta < 4 || n_theta > MAX_NTHETA)) {
+    set_error("n_theta must be 0 or in 4..32");
+    return BEM_ERR_INVALID_ARG;
+  }
+  if (n == 0) return BEM_OK;
+  STBEM_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  DevBuf<double> dx, dt, dout;
+  DevBuf<int32_t> dsv;
+  TRY(dx.alloc(4 * n)); TRY(dt.alloc(16 * n)); TRY(dout.alloc(n)); TRY(dsv.alloc(4 * n));
+  STBEM_CUDA(cudaMemcpyAsync(dx.p, x4, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, s));
+  STBEM_CUDA(cudaMemcpyAsync(dt.p, tets, sizeof(double) * 16 * n, cudaMemcpyHostToDevice, s));
+  STBEM_CUDA(cudaMemcpyAsync(dsv.p, tet_sv, sizeof(int32_t) * 4 * n, cudaMemcpyHostToDevice, s));
+  TRY(inner_potentials(n, dx.p, dt.p, dsv.p, precision, n_theta, dout.p, s));
+  STBEM_CUDA(cudaMemcpyAsync(out, dout.p, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  STBEM_CUDA(cudaStreamSynchronize(s));
+  return BEM_OK;
+}
+
+}  // extern "C"

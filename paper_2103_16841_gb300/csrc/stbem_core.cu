@@ -1,0 +1,964 @@
+// Kernels of the light-cone-clipped single-layer Galerkin assembly.
+//
+// Work decomposition: the matrix is cut into blocks (I, J) of panels over
+// spatial triangle ("column") I times panels over column J. A persistent
+// grid pops blocks from a device counter. For every face F with nu_{F,t} != 0
+// over column I and every outer point x_q on F (composite midpoint rule,
+// Fig. int_tri_mid), the kernel evaluates the potentials W of the faces over
+// column J that the backward light cone of x_q cuts, and forms
+//     U[F][j] = sum_q V 1_{sigma_j}(x_q) = sum_q (W_lo(j)(x_q) - W_hi(j)(x_q)),
+// then the entries A_ij = |K_I| / m_Q^2 * (U[F_lo(i)][j] - U[F_hi(i)][j])
+// (eq. int_bform with nu_{F,t}|F| = -|K| on the lower face, +|K| on the upper).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "stbem_internal.h"
+
+namespace stbem {
+
+bem_status upload_gauss_tables() {
+  std::vector<double> X(MAX_NTHETA * (MAX_NTHETA + 1) / 2), W(X.size());
+  for (int n = 1; n <= MAX_NTHETA; ++n) {
+    int off = n * (n - 1) / 2;
+    for (int i = 0; i < n; ++i) {
+      double z = std::cos(STBEM_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+      for (int it = 0; it < 100; ++it) {
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+          double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+          p0 = p1;
+          p1 = p2;
+        }
+        if (n == 1) { p1 = z; p0 = 1.0; }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        double dz = p1 / dp;
+        z -= dz;
+        if (std::fabs(dz) < 1e-16) break;
+      }
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      X[off + i] = z;
+      W[off + i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+  }
+  std::copy(X.begin(), X.end(), h_gl_x);
+  std::copy(W.begin(), W.end(), h_gl_w);
+  STBEM_CUDA(cudaMemcpyToSymbol(c_gl_x, X.data(), X.size() * sizeof(double)));
+  STBEM_CUDA(cudaMemcpyToSymbol(c_gl_w, W.data(), W.size() * sizeof(double)));
+  return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Staging: column frames, face gradients, panel balls
+// ---------------------------------------------------------------------------
+__global__ void k_col_geom(int64_t n_col, const double* sv_xyz, const int32_t* corner_sv, ColGeom* out) {
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n_col) return;
+  const int32_t* s = corner_sv + 3 * c;
+  make_colgeom(sv_xyz + 3 * s[0], sv_xyz + 3 * s[1], sv_xyz + 3 * s[2], out[c]);
+}
+
+// surf_p [n_surf][3] corner times; surf_col [n_surf]
+__global__ void k_surf_geom(int64_t n_surf, const ColGeom* cols, const double* surf_p, const int32_t* surf_col,
+                            SurfDev* out) {
+  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n_surf) return;
+  SurfDev S;
+  S.col = surf_col[s];
+  S.pad = 0;
+  for (int k = 0; k < 3; ++k) S.f.p[k] = surf_p[3 * s + k];
+  face_gradient(cols[S.col], S.f);
+  out[s] = S;
+}
+
+// tet_vx [n_tet][4][4]: the panel's vertices (t,x,y,z) in the caller's order;
+// the 4D ball is formed in that order with the fixed operation order of the
+// sparsity contract: centre (((X0+X1)+X2)+X3)/4, radius max_v |X_v - c|.
+__global__ void k_tet_ball(int64_t n_tet, const double* tet_vx, TetDev* tets) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_tet) return;
+  const double* X = tet_vx + 16 * i;
+  double c[4];
+  for (int d = 0; d < 4; ++d)
+    c[d] = __ddiv_rn(__dadd_rn(__dadd_rn(__dadd_rn(X[d], X[4 + d]), X[8 + d]), X[12 + d]), 4.0);
+  double mx = 0.0;
+  for (int v = 0; v < 4; ++v) {
+    double a = __dsub_rn(X[4 * v + 0], c[0]), b = __dsub_rn(X[4 * v + 1], c[1]);
+    double e = __dsub_rn(X[4 * v + 2], c[2]), f = __dsub_rn(X[4 * v + 3], c[3]);
+    double l = __dsqrt_rn(__dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(e, e)),
+                                    __dmul_rn(f, f)));
+    if (l > mx) mx = l;
+  }
+  for (int d = 0; d < 4; ++d) tets[i].ball[d] = c[d];
+  tets[i].ball[4] = mx;
+}
+
+bem_status mesh_device_geometry(bem_mesh* m, const double* d_sv_xyz, const int32_t* d_col_corner_sv,
+                                const double* d_tet_vx, const int32_t* d_surf_col, const double* d_surf_p) {
+  cudaStream_t s = m->ctx->stream;
+  int th = 128;
+  k_col_geom<<<(unsigned)((m->n_col + th - 1) / th), th, 0, s>>>(m->n_col, d_sv_xyz, d_col_corner_sv, m->d_col);
+  k_surf_geom<<<(unsigned)((m->n_surf + th - 1) / th), th, 0, s>>>(m->n_surf, m->d_col, d_surf_p, d_surf_col,
+                                                                   m->d_surf);
+  k_tet_ball<<<(unsigned)((m->n_tet + th - 1) / th), th, 0, s>>>(m->n_tet, d_tet_vx, m->d_tet);
+  STBEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Outer points (Fig. int_tri_mid): canonical corner order (ascending spatial
+// id) and x = (A + xi1 (B - A)) + xi2 (C - A) without fused operations.
+// ---------------------------------------------------------------------------
+__global__ void k_outer_points(int64_t n_surf, int mq, const ColGeom* cols, const SurfDev* surf, double* pts,
+                               double* trange) {
+  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n_surf) return;
+  const SurfDev S = surf[s];
+  const ColGeom& G = cols[S.col];
+  double A[4] = {S.f.p[0], G.X[0][0], G.X[0][1], G.X[0][2]};
+  double B[4] = {S.f.p[1], G.X[1][0], G.X[1][1], G.X[1][2]};
+  double C[4] = {S.f.p[2], G.X[2][0], G.X[2][1], G.X[2][2]};
+  int nq = mq * mq;
+  double* out = pts + (int64_t)s * nq * 4;
+  double tlo = 1e300, thi = -1e300;
+  int n = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    double off = pass == 0 ? 1.0 / 3.0 : 2.0 / 3.0;
+    for (int i = 0; i < mq; ++i)
+      for (int j = 0; i + j <= mq - 1 - pass; ++j) {
+        double x1 = __ddiv_rn(__dadd_rn((double)i, off), (double)mq);
+        double x2 = __ddiv_rn(__dadd_rn((double)j, off), (double)mq);
+        for (int d = 0; d < 4; ++d) {
+          double p = __dadd_rn(A[d], __dmul_rn(x1, __dsub_rn(B[d], A[d])));
+          out[4 * n + d] = __dadd_rn(p, __dmul_rn(x2, __dsub_rn(C[d], A[d])));
+        }
+        tlo = fmin(tlo, out[4 * n]);
+        thi = fmax(thi, out[4 * n]);
+        ++n;
+      }
+  }
+  trange[2 * s] = tlo;
+  trange[2 * s + 1] = thi;
+}
+
+bem_status op_outer_points(bem_operator* op, cudaStream_t s) {
+  const bem_mesh* m = op->mesh;
+  int th = 128;
+  k_outer_points<<<(unsigned)((m->n_surf + th - 1) / th), th, 0, s>>>(m->n_surf, op->mq, m->d_col, m->d_surf,
+                                                                      op->d_pts, op->d_pts_trange);
+  STBEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sparsity predicate for one outer point and one panel (the contract):
+//   C1  tau_min(j) < t_q
+//   C2  max_b |x_q - y_b| - (t_q - tau_b) >= 0
+//   C3  not (phi_Xi(x_q - c_j) - d_r(|x_q - c_j|) > 0)     (Theorem phi_xi_sphere)
+// FP64 values with the contract's operation order decide; an FP32 estimate
+// with a rigorous error margin settles the clear cases first.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double dist3x(const double* a, const double* b) {
+  double dx = __dsub_rn(a[0], b[0]), dy = __dsub_rn(a[1], b[1]), dz = __dsub_rn(a[2], b[2]);
+  return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+}
+__device__ __forceinline__ float dist3f(const float* a, const float* b) {
+  float dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+  return sqrtf(dx * dx + dy * dy + dz * dz);
+}
+
+struct TetSm {       // panel data kept in shared memory for a block
+  double tmin, pmax;
+  double vt[4];
+  double ball[5];
+  int32_t lo, hi, dup, pad;
+};
+
+__device__ bool c2_exact(const double* x, const TetSm& T, const ColGeom& G) {
+  double mx = -INFINITY;
+  for (int b = 0; b < 4; ++b) {
+    int k = b < 3 ? b : T.dup;
+    double v = __dsub_rn(dist3x(x + 1, G.X[k]), __dsub_rn(x[0], T.vt[b]));
+    if (v > mx) mx = v;
+  }
+  return mx >= 0.0;
+}
+__device__ bool c3_fail_exact(const double* x, const TetSm& T) {
+  double al = dist3x(x + 1, T.ball + 1);
+  double phi = __dsub_rn(al, __dsub_rn(x[0], T.ball[0]));
+  double rj = T.ball[4];
+  double s2 = __dsqrt_rn(2.0);
+  double dr = (al < __ddiv_rn(rj, s2)) ? __dadd_rn(al, __dsqrt_rn(__dsub_rn(__dmul_rn(rj, rj), __dmul_rn(al, al))))
+                                       : __dmul_rn(rj, s2);
+  return __dsub_rn(phi, dr) > 0.0;
+}
+
+__device__ bool point_sees(const double* x, const float* xf, const TetSm& T, const ColGeom& G, const float (*Xf)[3],
+                           float margin) {
+  if (!(T.tmin < x[0])) return false;  // C1
+  // C2
+  {
+    bool sure_true = false, sure_false = true;
+    for (int b = 0; b < 4; ++b) {
+      int k = b < 3 ? b : T.dup;
+      float v = dist3f(xf + 1, Xf[k]) - (xf[0] - (float)T.vt[b]);
+      if (v > margin) sure_true = true;
+      if (!(v < -margin)) sure_false = false;
+    }
+    if (!sure_true) {
+      if (sure_false) return false;
+      if (!c2_exact(x, T, G)) return false;
+    }
+  }
+  // C3
+  {
+    float bc[3] = {(float)T.ball[1], (float)T.ball[2], (float)T.ball[3]};
+    float al = dist3f(xf + 1, bc);
+    float phi = al - (xf[0] - (float)T.ball[0]);
+    float rj = (float)T.ball[4];
+    float dr = (al < rj * 0.70710678f) ? al + sqrtf(fmaxf(rj * rj - al * al, 0.f)) : rj * 1.41421356f;
+    float v = phi - dr;
+    if (v > margin) return false;
+    if (!(v < -margin)) {
+      if (c3_fail_exact(x, T)) return false;
+    }
+  }
+  return true;
+}
+
+// shared-memory image of column J
+struct ColSm {
+  ColGeom G;
+  float Xf[3][3];
+  int32_t tet0, ntet, surf0, nsurf;
+  double rmax;  // max panel ball radius
+};
+
+// Trial window of column J for a face with outer-point time range [tlo, thi]:
+// panels outside [jlo, jhi) are certainly outside the pattern.
+__device__ inline void trial_window(const ColSm& C, const TetSm* T, double tlo, double thi, double Dmax,
+                                    double Dmin_lo, double S, int& jlo, int& jhi) {
+  double lim1 = tlo - Dmax * (1.0 + 1e-12) - 1e-12 * S;
+  int a = 0, b = C.ntet;  // first j with pmax >= lim1
+  while (a < b) { int m = (a + b) >> 1; if (T[m].pmax < lim1) a = m + 1; else b = m; }
+  jlo = a;
+  double lim2 = thi + fmin(0.0, C.rmax * 1.41421356237309515 * (1.0 + 1e-12) - Dmin_lo * (1.0 - 1e-12)) + 1e-12 * S;
+  a = jlo; b = C.ntet;    // first j with tmin >= lim2
+  while (a < b) { int m = (a + b) >> 1; if (T[m].tmin < lim2) a = m + 1; else b = m; }
+  jhi = a;
+}
+
+__device__ inline void col_pair_bounds(const ColGeom& GI, const ColGeom& GJ, double& Dmax, double& Dmin_lo) {
+  Dmax = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double dx = GI.X[a][0] - GJ.X[b][0], dy = GI.X[a][1] - GJ.X[b][1], dz = GI.X[a][2] - GJ.X[b][2];
+      Dmax = fmax(Dmax, sqrt(dx * dx + dy * dy + dz * dz));
+    }
+  double dx = GI.ctr[0] - GJ.ctr[0], dy = GI.ctr[1] - GJ.ctr[1], dz = GI.ctr[2] - GJ.ctr[2];
+  Dmin_lo = fmax(0.0, sqrt(dx * dx + dy * dy + dz * dz) - GI.rad - GJ.rad);
+}
+
+struct BlockCtx {
+  int64_t n_col;
+  int mq, nq, n_theta, prec;
+  ArcRule rule;
+  float margin;
+  double S;
+  const ColGeom* cols;
+  const int32_t* col_tet_begin;
+  const int32_t* col_surf_begin;
+  const SurfDev* surf;
+  const TetDev* tets;
+  const double* pts;
+  const double* trange;
+  int32_t* bw;
+  int64_t* bnnz;
+  const int64_t* boff;
+  const int64_t* rsoff;
+  int32_t* rs;
+  double* val;
+  float* val32;
+  double* uscratch;     // [gridDim][max_surf][max_tet]
+  int max_surf, max_tet;
+  unsigned long long* counter;
+};
+
+// cooperative load of column J into shared memory
+__device__ void load_column(const BlockCtx& B, int64_t J, ColSm& C, TetSm* T, FaceGeom* Fs) {
+  if (threadIdx.x == 0) {
+    C.G = B.cols[J];
+    for (int k = 0; k < 3; ++k)
+      for (int i = 0; i < 3; ++i) C.Xf[k][i] = (float)C.G.X[k][i];
+    C.tet0 = B.col_tet_begin[J];
+    C.ntet = B.col_tet_begin[J + 1] - C.tet0;
+    C.surf0 = B.col_surf_begin[J];
+    C.nsurf = B.col_surf_begin[J + 1] - C.surf0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < C.ntet; j += blockDim.x) {
+    const TetDev& D = B.tets[C.tet0 + j];
+    TetSm t;
+    t.tmin = D.tmin; t.pmax = D.pmax;
+    for (int k = 0; k < 4; ++k) t.vt[k] = D.vt[k];
+    for (int k = 0; k < 5; ++k) t.ball[k] = D.ball[k];
+    t.lo = D.lo - C.surf0; t.hi = D.hi - C.surf0; t.dup = D.dup; t.pad = 0;
+    T[j] = t;
+  }
+  for (int s = threadIdx.x; s < C.nsurf; s += blockDim.x) Fs[s] = B.surf[C.surf0 + s].f;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int j = 0; j < C.ntet; ++j) r = fmax(r, T[j].ball[4]);
+    C.rmax = r;
+  }
+  __syncthreads();
+}
+
+// pattern bits of one face f' (global id) of column I against column J.
+// Warp-cooperative; writes bits[0..words) and returns the trial window.
+__device__ void face_bits(const BlockCtx& B, const ColSm& C, const TetSm* T, int64_t fglob, double Dmax,
+                          double Dmin_lo, uint32_t* bits, int words, int& jlo, int& jhi) {
+  int lane = threadIdx.x & 31;
+  double tlo = B.trange[2 * fglob], thi = B.trange[2 * fglob + 1];
+  trial_window(C, T, tlo, thi, Dmax, Dmin_lo, B.S, jlo, jhi);
+  for (int w = lane; w < words; w += 32) bits[w] = 0u;
+  __syncwarp();
+  const double* P = B.pts + fglob * B.nq * 4;
+  for (int j0 = jlo; j0 < jhi; j0 += 32) {
+    int j = j0 + lane;
+    bool hit = false;
+    if (j < jhi) {
+      for (int q = 0; q < B.nq && !hit; ++q) {
+        const double* x = P + 4 * q;
+        float xf[4] = {(float)x[0], (float)x[1], (float)x[2], (float)x[3]};
+        hit = point_sees(x, xf, T[j], C.G, C.Xf, B.margin);
+      }
+    }
+    unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0 && m) {
+      // j0 may not be word aligned: scatter bit by bit
+      for (int l = 0; l < 32; ++l)
+        if (m & (1u << l)) bits[(j0 + l) >> 5] |= 1u << ((j0 + l) & 31);
+    }
+    __syncwarp();
+  }
+}
+
+__device__ inline int64_t pop_block(const BlockCtx& B) {
+  __shared__ unsigned long long s_b;
+  if (threadIdx.x == 0) s_b = atomicAdd(B.counter, 1ull);
+  __syncthreads();
+  int64_t b = (int64_t)s_b;
+  __syncthreads();
+  return b;
+}
+
+// Pass 1: band width and pattern count of every column block.
+__global__ void __launch_bounds__(128) k_pattern_blocks(BlockCtx B) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ColSm C;
+  TetSm* T = reinterpret_cast<TetSm*>(smem);
+  FaceGeom* Fs = reinterpret_cast<FaceGeom*>(T + B.max_tet);
+  uint32_t* bits = reinterpret_cast<uint32_t*>(Fs + B.max_surf);
+  const int words = (B.max_tet + 31) / 32;
+  __shared__ int s_w[4];
+  __shared__ unsigned long long s_n[4];
+  const int64_t nblk = B.n_col * B.n_col;
+  for (;;) {
+    int64_t b = pop_block(B);
+    if (b >= nblk) break;
+    int64_t I = b / B.n_col, J = b % B.n_col;
+    load_column(B, J, C, T, Fs);
+    const ColGeom GI = B.cols[I];
+    double Dmax, Dmin_lo;
+    col_pair_bounds(GI, C.G, Dmax, Dmin_lo);
+    int s0 = B.col_surf_begin[I], ns = B.col_surf_begin[I + 1] - s0;
+    int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int f = warp; f < ns; f += nw) {
+      int jlo, jhi;
+      face_bits(B, C, T, s0 + f, Dmax, Dmin_lo, bits + f * words, words, jlo, jhi);
+    }
+    __syncthreads();
+    int t0 = B.col_tet_begin[I], nt = B.col_tet_begin[I + 1] - t0;
+    int wmax = 0;
+    unsigned long long cnt = 0;
+    for (int r = threadIdx.x; r < nt; r += blockDim.x) {
+      const TetDev& D = B.tets[t0 + r];
+      int lo = D.lo - s0, hi = D.hi - s0;
+      int first = -1, last = -1;
+      for (int w = 0; w < words; ++w) {
+        uint32_t m = bits[lo * words + w] | bits[hi * words + w];
+        cnt += __popc(m);
+        if (m) {
+          if (first < 0) first = 32 * w + __ffs(m) - 1;
+          last = 32 * w + 31 - __clz(m);
+        }
+      }
+      if (first >= 0) wmax = max(wmax, last - first + 1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+      cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if ((threadIdx.x & 31) == 0) { s_w[threadIdx.x >> 5] = wmax; s_n[threadIdx.x >> 5] = cnt; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int w = 0;
+      unsigned long long n = 0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { w = max(w, s_w[i]); n += s_n[i]; }
+      B.bw[b] = w;
+      B.bnnz[b] = (int64_t)n;
+    }
+    __syncthreads();
+  }
+}
+
+// Pass 2: quadrature and assembly of every non-empty block.
+template <bool FP32>
+__global__ void __launch_bounds__(128) k_quad_blocks(BlockCtx B) {
+  typedef typename std::conditional<FP32, float, double>::type R;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ColSm C;
+  __shared__ ColR<R> CR;
+  TetSm* T = reinterpret_cast<TetSm*>(smem);
+  FaceGeom* Fs = reinterpret_cast<FaceGeom*>(T + B.max_tet);
+  uint32_t* bits = reinterpret_cast<uint32_t*>(Fs + B.max_surf);
+  const int words = (B.max_tet + 31) / 32;
+  PointCol* pc = reinterpret_cast<PointCol*>(bits + ((B.max_surf * words + 3) & ~3));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  PointCol* mypc = pc + warp * B.nq;
+  R* Wsc = reinterpret_cast<R*>(reinterpret_cast<double*>(pc + nw * B.nq) + (size_t)warp * B.nq * B.max_surf);
+  uint16_t* mycut = reinterpret_cast<uint16_t*>(reinterpret_cast<double*>(pc + nw * B.nq) +
+                                                (size_t)nw * B.nq * B.max_surf) + (size_t)warp * B.nq * B.max_surf;
+  FaceF* Ff = reinterpret_cast<FaceF*>(reinterpret_cast<uint16_t*>(reinterpret_cast<double*>(pc + nw * B.nq) +
+                                                                   (size_t)nw * B.nq * B.max_surf) +
+                                       ((size_t)nw * B.nq * B.max_surf + 7) / 8 * 8);
+  R* U = reinterpret_cast<R*>(B.uscratch) + (size_t)blockIdx.x * B.max_surf * B.max_tet;
+  const int64_t nblk = B.n_col * B.n_col;
+  for (;;) {
+    int64_t b = pop_block(B);
+    if (b >= nblk) break;
+    int W = B.bw[b];
+    if (W == 0) continue;
+    int64_t I = b / B.n_col, J = b % B.n_col;
+    load_column(B, J, C, T, Fs);
+    if (threadIdx.x == 0) make_colr<R>(C.G, CR);
+    if (FP32)
+      for (int s = threadIdx.x; s < C.nsurf; s += blockDim.x) make_facef(Fs[s], Ff[s]);
+    __syncthreads();
+    const ColGeom GI = B.cols[I];
+    double Dmax, Dmin_lo;
+    col_pair_bounds(GI, C.G, Dmax, Dmin_lo);
+    const int s0 = B.col_surf_begin[I], ns = B.col_surf_begin[I + 1] - s0;
+    const int ntJ = C.ntet;
+    const float fdiam = (float)C.G.diam;
+    for (int f = warp; f < ns; f += nw) {
+      int jlo, jhi;
+      const int64_t fg = s0 + f;
+      face_bits(B, C, T, fg, Dmax, Dmin_lo, bits + f * words, words, jlo, jhi);
+      R* Urow = U + (size_t)f * B.max_tet;
+      for (int j = lane; j < ntJ; j += 32) Urow[j] = R(0);
+      if (jhi <= jlo) { __syncwarp(); continue; }
+      // surface window of the trial panels
+      int slo = 1 << 30, shi = -1;
+      for (int j = jlo + lane; j < jhi; j += 32) {
+        slo = min(slo, min(T[j].lo, T[j].hi));
+        shi = max(shi, max(T[j].lo, T[j].hi));
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        slo = min(slo, __shfl_xor_sync(0xffffffffu, slo, o));
+        shi = max(shi, __shfl_xor_sync(0xffffffffu, shi, o));
+      }
+      const int nsw = shi - slo + 1;
+      // per-point geometry against column J
+      const double* P = B.pts + fg * B.nq * 4;
+      for (int q = lane; q < B.nq; q += 32) point_col(P + 4 * q, C.G, mypc[q], FP32);
+      __syncwarp();
+      // pass 1: classify every (point, face) pair from the cone-function values
+      // at the corners; fully lit and dark pairs are final, cut pairs are listed
+      const int nit = B.nq * nsw;
+      int ncut = 0;
+      for (int base = 0; base < nit; base += 32) {
+        int it = base + lane;
+        bool cut = false;
+        if (it < nit) {
+          int q = it / nsw, s = it - q * nsw;
+          int cls;
+          if (FP32) {
+            float Fv[3], cc = 0.f;
+            cls = face_class_mixed(mypc[q], Ff[slo + s], Fv, cc, fdiam);
+          } else {
+            double Fv[3], cc = 0.0;
+            cls = face_class(C.G, mypc[q], Fs[slo + s], Fv, cc);
+          }
+          if (cls == FACE_CUT) cut = true;
+          else Wsc[q * B.max_surf + s] = cls == FACE_LIT ? (R)mypc[q].Wst : R(0);
+        }
+        unsigned mk = __ballot_sync(0xffffffffu, cut);
+        if (cut) mycut[ncut + __popc(mk & ((1u << lane) - 1u))] = (uint16_t)it;
+        ncut += __popc(mk);
+      }
+      __syncwarp();
+      // pass 2: the cut pairs, converged across the warp
+      for (int k = lane; k < ncut; k += 32) {
+        int it = mycut[k];
+        int q = it / nsw, s = it - q * nsw;
+        FaceCutIn<R> in;
+        if constexpr (FP32) {
+          float Fv[3], cc = 0.f;
+          face_class_mixed(mypc[q], Ff[slo + s], Fv, cc, fdiam);
+          cut_in_mixed(mypc[q], Ff[slo + s], Fv, cc, Fs[slo + s], in);
+        } else {
+          double Fv[3], cc = 0.0;
+          face_class(C.G, mypc[q], Fs[slo + s], Fv, cc);
+          cut_in_fp64(mypc[q], Fs[slo + s], Fv, cc, in);
+        }
+        Wsc[q * B.max_surf + s] = (R)face_cut<R>(CR, mypc[q], in, B.rule);
+      }
+      __syncwarp();
+      const uint32_t* fb = bits + f * words;
+      for (int j = jlo + lane; j < jhi; j += 32) {
+        if (!((fb[j >> 5] >> (j & 31)) & 1u)) continue;
+        int lo = T[j].lo - slo, hi = T[j].hi - slo;
+        R u = R(0);
+        for (int q = 0; q < B.nq; ++q) u += Wsc[q * B.max_surf + lo] - Wsc[q * B.max_surf + hi];
+        Urow[j] = u;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    // entries of the block rows
+    const int t0 = B.col_tet_begin[I], nt = B.col_tet_begin[I + 1] - t0;
+    const R scale = (R)(GI.area / (4.0 * STBEM_PI * B.nq));
+    const int64_t voff = B.boff[b], roff = B.rsoff[b];
+    for (int r = threadIdx.x; r < nt; r += blockDim.x) {
+      const TetDev& D = B.tets[t0 + r];
+      int lo = D.lo - s0, hi = D.hi - s0;
+      int first = -1;
+      for (int w = 0; w < words && first < 0; ++w) {
+        uint32_t m = bits[lo * words + w] | bits[hi * words + w];
+        if (m) first = 32 * w + __ffs(m) - 1;
+      }
+      if (first < 0) first = 0;
+      B.rs[roff + r] = C.tet0 + first;
+      const R* Ulo = U + (size_t)lo * B.max_tet;
+      const R* Uhi = U + (size_t)hi * B.max_tet;
+      for (int w = 0; w < W; ++w) {
+        int j = first + w;
+        R v = R(0);
+        if (j < ntJ) v = scale * (Ulo[j] - Uhi[j]);
+        B.val[voff + (int64_t)w * nt + r] = (double)v;
+        if (B.val32) B.val32[voff + (int64_t)w * nt + r] = (float)v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+static size_t block_smem(const bem_operator* op, bool quad) {
+  const bem_mesh* m = op->mesh;
+  int words = (m->max_col_tets + 31) / 32;
+  size_t s = sizeof(TetSm) * m->max_col_tets + sizeof(FaceGeom) * m->max_col_surf;
+  s += sizeof(uint32_t) * ((m->max_col_surf * words + 3) & ~3);
+  if (quad) {
+    s += sizeof(PointCol) * 4 * op->nq;
+    s += sizeof(double) * 4 * op->nq * m->max_col_surf;
+    s += sizeof(uint16_t) * (((size_t)4 * op->nq * m->max_col_surf + 7) / 8 * 8);
+    s += sizeof(FaceF) * m->max_col_surf;
+  }
+  return s;
+}
+
+static int persistent_grid(const void* kern, size_t smem, int threads) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem);
+  if (per < 1) per = 1;
+  return sms * per;
+}
+
+static BlockCtx make_ctx(bem_operator* op) {
+  const bem_mesh* m = op->mesh;
+  BlockCtx B;
+  B.n_col = m->n_col;
+  B.mq = op->mq; B.nq = op->nq; B.n_theta = op->n_theta; B.prec = op->opts.precision;
+  B.rule = make_rule(op->opts.precision, op->n_theta);
+  B.S = m->coord_scale;
+  B.margin = (float)(1.6e-5 * m->coord_scale);  // > 4x the FP32 error bound of C2 and C3
+  B.cols = m->d_col; B.col_tet_begin = m->d_col_tet_begin; B.col_surf_begin = m->d_col_surf_begin;
+  B.surf = m->d_surf; B.tets = m->d_tet; B.pts = op->d_pts; B.trange = op->d_pts_trange;
+  B.bw = op->d_bw; B.bnnz = op->d_bnnz; B.boff = op->d_boff; B.rsoff = op->d_rsoff; B.rs = op->d_rs;
+  B.val = op->d_val; B.val32 = op->d_val32; B.uscratch = op->d_tmp;
+  B.max_surf = m->max_col_surf; B.max_tet = m->max_col_tets;
+  B.counter = nullptr;
+  return B;
+}
+
+static bem_status get_counter(const bem_operator* op, unsigned long long** out, cudaStream_t s) {
+  STBEM_CUDA(cudaMemsetAsync(op->d_counter, 0, sizeof(unsigned long long), s));
+  *out = op->d_counter;
+  return BEM_OK;
+}
+
+bem_status op_pattern(bem_operator* op, cudaStream_t s) {
+  BlockCtx B = make_ctx(op);
+  bem_status st = get_counter(op, &B.counter, s);
+  if (st != BEM_OK) return st;
+  size_t smem = block_smem(op, false);
+  STBEM_CUDA(cudaFuncSetAttribute(k_pattern_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int grid = persistent_grid((const void*)k_pattern_blocks, smem, 128);
+  k_pattern_blocks<<<grid, 128, smem, s>>>(B);
+  STBEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+int quad_grid(const bem_operator* op) {
+  size_t smem = block_smem(op, true);
+  if (op->opts.precision == BEM_PREC_MIXED) {
+    cudaFuncSetAttribute(k_quad_blocks<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return persistent_grid((const void*)k_quad_blocks<true>, smem, 128);
+  }
+  cudaFuncSetAttribute(k_quad_blocks<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return persistent_grid((const void*)k_quad_blocks<false>, smem, 128);
+}
+
+bem_status op_quadrature(bem_operator* op, cudaStream_t s) {
+  BlockCtx B = make_ctx(op);
+  bem_status st = get_counter(op, &B.counter, s);
+  if (st != BEM_OK) return st;
+  size_t smem = block_smem(op, true);
+  int grid = quad_grid(op);
+  if ((int64_t)grid * op->mesh->max_col_surf * op->mesh->max_col_tets > op->tmp_len) {
+    set_error("quadrature scratch too small");
+    return BEM_ERR_INTERNAL;
+  }
+  if (op->opts.precision == BEM_PREC_MIXED) k_quad_blocks<true><<<grid, 128, smem, s>>>(B);
+  else k_quad_blocks<false><<<grid, 128, smem, s>>>(B);
+  STBEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Matrix-vector product over the block-banded storage.
+// One CTA per test column I; G groups of R_I threads split the trial columns
+// J (g, g+G, ...), each thread owns one row; per block the band values are
+// read column-major (consecutive rows -> consecutive addresses).
+// ---------------------------------------------------------------------------
+template <typename V>
+__global__ void k_matvec(int64_t n_col, const int32_t* col_tet_begin, const int32_t* bw, const int64_t* boff,
+                         const int64_t* rsoff, const int32_t* rs, const V* val, const double* x, double* y,
+                         int64_t n_tet, int nrhs, int groups) {
+  extern __shared__ double red[];
+  const int64_t I = blockIdx.x;
+  const int t0 = col_tet_begin[I], nt = col_tet_begin[I + 1] - t0;
+  const int rows_pad = blockDim.x / groups;
+  const int g = threadIdx.x / rows_pad, r = threadIdx.x % rows_pad;
+  for (int rh = 0; rh < nrhs; ++rh) {
+    const double* xr = x + (int64_t)rh * n_tet;
+    double acc = 0.0;
+    if (r < nt) {
+      for (int64_t J = g; J < n_col; J += groups) {
+        int64_t b = I * n_col + J;
+        int W = bw[b];
+        if (W == 0) continue;
+        int64_t vo = boff[b];
+        int start = rs[rsoff[b] + r];
+        int jend = col_tet_begin[J + 1];
+        const V* v = val + vo + r;
+        for (int w = 0; w < W; ++w) {
+          int j = start + w;
+          j = j < jend ? j : jend - 1;
+          acc += (double)v[(int64_t)w * nt] * xr[j];
+        }
+      }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (g == 0 && r < nt) {
+      double s = 0.0;
+      for (int k = 0; k < groups; ++k) s += red[k * rows_pad + r];
+      y[(int64_t)rh * n_tet + t0 + r] = s;
+    }
+    __syncthreads();
+  }
+}
+
+bem_status op_matvec(const bem_operator* op, const double* x, double* y, int nrhs, bool fp32, cudaStream_t s) {
+  const bem_mesh* m = op->mesh;
+  int rows_pad = ((m->max_col_tets + 31) / 32) * 32;
+  int groups = std::max(1, std::min(8, 512 / rows_pad));
+  int threads = rows_pad * groups;
+  size_t smem = sizeof(double) * threads;
+  if (fp32) {
+    if (!op->d_val32) { set_error("operator has no FP32 values (store_fp32 = 0)"); return BEM_ERR_INVALID_ARG; }
+    k_matvec<float><<<(unsigned)m->n_col, threads, smem, s>>>(m->n_col, m->d_col_tet_begin, op->d_bw, op->d_boff,
+                                                               op->d_rsoff, op->d_rs, op->d_val32, x, y, m->n_tet,
+                                                               nrhs, groups);
+  } else {
+    k_matvec<double><<<(unsigned)m->n_col, threads, smem, s>>>(m->n_col, m->d_col_tet_begin, op->d_bw, op->d_boff,
+                                                                op->d_rsoff, op->d_rs, op->d_val, x, y, m->n_tet,
+                                                                nrhs, groups);
+  }
+  STBEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Entry lookup (internal indices) and pattern CSR export
+// ---------------------------------------------------------------------------
+__global__ void k_entries(int64_t n, const int32_t* ij, const int32_t* iperm_unused, const TetDev* tets, int64_t n_col,
+                          const int32_t* col_tet_begin, const int32_t* bw, const int64_t* boff, const int64_t* rsoff,
+                          const int32_t* rs, const double* val, double* out) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int i = ij[2 * k], j = ij[2 * k + 1];
+  int I = tets[i].col, J = tets[j].col;
+  int64_t b = (int64_t)I * n_col + J;
+  int W = bw[b];
+  double v = 0.0;
+  if (W > 0) {
+    int r = i - col_tet_begin[I];
+    int nt = col_tet_begin[I + 1] - col_tet_begin[I];
+    int start = rs[rsoff[b] + r];
+    int w = j - start;
+    if (w >= 0 && w < W) v = val[boff[b] + (int64_t)w * nt + r];
+  }
+  out[k] = v;
+}
+
+bem_status op_entries(const bem_operator* op, int64_t n, const int32_t* d_ij, double* d_out, cudaStream_t s) {
+  const bem_mesh* m = op->mesh;
+  if (n == 0) return BEM_OK;
+  k_entries<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, d_ij, nullptr, m->d_tet, m->n_col, m->d_col_tet_begin,
+                                                       op->d_bw, op->d_boff, op->d_rsoff, op->d_rs, op->d_val, d_out);
+  STBEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+// Pattern rows (internal numbering): count pass, then fill pass (columns are
+// written in internal order; the caller permutes and sorts).
+__global__ void __launch_bounds__(128) k_pattern_rows(BlockCtx B, int64_t* rowcount, const int64_t* rowptr,
+                                                      int32_t* cols, int fill) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ColSm C;
+  TetSm* T = reinterpret_cast<TetSm*>(smem);
+  FaceGeom* Fs = reinterpret_cast<FaceGeom*>(T + B.max_tet);
+  uint32_t* bits = reinterpret_cast<uint32_t*>(Fs + B.max_surf);
+  const int words = (B.max_tet + 31) / 32;
+  const int64_t nblk = B.n_col * B.n_col;
+  for (;;) {
+    int64_t b = pop_block(B);
+    if (b >= nblk) break;
+    if (B.bw[b] == 0) continue;
+    int64_t I = b / B.n_col, J = b % B.n_col;
+    load_column(B, J, C, T, Fs);
+    const ColGeom GI = B.cols[I];
+    double Dmax, Dmin_lo;
+    col_pair_bounds(GI, C.G, Dmax, Dmin_lo);
+    int s0 = B.col_surf_begin[I], ns = B.col_surf_begin[I + 1] - s0;
+    int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int f = warp; f < ns; f += nw) {
+      int jlo, jhi;
+      face_bits(B, C, T, s0 + f, Dmax, Dmin_lo, bits + f * words, words, jlo, jhi);
+    }
+    __syncthreads();
+    int t0 = B.col_tet_begin[I], nt = B.col_tet_begin[I + 1] - t0;
+    for (int r = threadIdx.x; r < nt; r += blockDim.x) {
+      const TetDev& D = B.tets[t0 + r];
+      int lo = D.lo - s0, hi = D.hi - s0;
+      int cnt = 0;
+      for (int w = 0; w < words; ++w) cnt += __popc(bits[lo * words + w] | bits[hi * words + w]);
+      if (!cnt) continue;
+      unsigned long long pos = atomicAdd((unsigned long long*)&rowcount[t0 + r], (unsigned long long)cnt);
+      if (fill) {
+        for (int w = 0; w < words; ++w) {
+          uint32_t m = bits[lo * words + w] | bits[hi * words + w];
+          while (m) {
+            int l = __ffs(m) - 1;
+            m &= m - 1;
+            cols[rowptr[t0 + r] + (int64_t)pos++] = C.tet0 + 32 * w + l;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+bem_status op_pattern_csr(const bem_operator* op, int64_t* d_rowcount, int64_t* d_rowptr, int32_t* d_cols, bool fill,
+                          cudaStream_t s) {
+  BlockCtx B = make_ctx(const_cast<bem_operator*>(op));
+  bem_status st = get_counter(op, &B.counter, s);
+  if (st != BEM_OK) return st;
+  size_t smem = block_smem(op, false);
+  STBEM_CUDA(cudaFuncSetAttribute(k_pattern_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int grid = persistent_grid((const void*)k_pattern_rows, smem, 128);
+  k_pattern_rows<<<grid, 128, smem, s>>>(B, d_rowcount, d_rowptr, d_cols, fill ? 1 : 0);
+  STBEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Right-hand side: b_i = int_K [g(P_lo(y), y) - g(P_hi(y), y)] dA
+// (= -sum_F nu_{F,t} int_F g dS, eq. int_bform with A = Id). K is split into
+// 4^k congruent sub-triangles, k chosen so that a sub-triangle spans at most
+// half the data's length scale (pulse width, or 0.5 for the sin^2 data), and
+// each gets a Duffy-collapsed 8 x 8 Gauss-Legendre rule.
+// ---------------------------------------------------------------------------
+__device__ inline double data_g(int kind, const double* prm, double t, const double* x) {
+  if (kind == BEM_DATA_SIN2_UNIFORM) {
+    if (!(t > 0.0 && t < 2.0)) return 0.0;
+    double s = sin(0.5 * STBEM_PI * t);
+    return s * s;
+  }
+  double a = (t - (x[0] * prm[0] + x[1] * prm[1] + x[2] * prm[2]) - prm[3]) / prm[4];
+  return exp(-a * a);
+}
+
+__device__ inline double rhs_subtri(const ColGeom& G, const FaceGeom& Flo, const FaceGeom& Fhi, int kind,
+                                    const double* prm, const double* B0, const double* B1, const double* B2) {
+  const int n = 8;
+  const double* X = gl_x() + n * (n - 1) / 2;
+  const double* Wt = gl_w() + n * (n - 1) / 2;
+  double acc = 0.0;
+  for (int a = 0; a < n; ++a) {
+    double u = 0.5 * (X[a] + 1.0), wu = 0.5 * Wt[a];
+    for (int c = 0; c < n; ++c) {
+      double v = 0.5 * (X[c] + 1.0), wv = 0.5 * Wt[c];
+      double m0 = 1.0 - u, m1 = u * (1.0 - v), m2 = u * v;   // Duffy: Jacobian 2 |sub| u
+      double l[3];
+      for (int k = 0; k < 3; ++k) l[k] = m0 * B0[k] + m1 * B1[k] + m2 * B2[k];
+      double y[3];
+      for (int k = 0; k < 3; ++k) y[k] = l[0] * G.X[0][k] + l[1] * G.X[1][k] + l[2] * G.X[2][k];
+      double tlo = l[0] * Flo.p[0] + l[1] * Flo.p[1] + l[2] * Flo.p[2];
+      double thi = l[0] * Fhi.p[0] + l[1] * Fhi.p[1] + l[2] * Fhi.p[2];
+      acc += wu * wv * u * (data_g(kind, prm, tlo, y) - data_g(kind, prm, thi, y));
+    }
+  }
+  return acc;
+}
+
+__global__ void k_rhs(int64_t n_tet, const TetDev* tets, const SurfDev* surf, const ColGeom* cols, int kind, int nrhs,
+                      const double* params, double* b) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_tet) return;
+  const TetDev D = tets[i];
+  const ColGeom& G = cols[D.col];
+  const FaceGeom Flo = surf[D.lo].f, Fhi = surf[D.hi].f;
+  for (int r = 0; r < nrhs; ++r) {
+    const double* prm = params ? params + 5 * r : nullptr;
+    double scale = kind == BEM_DATA_PULSE ? 0.5 * prm[4] : 0.5;
+    int lev = 0;
+    while (lev < 4 && G.diam / (double)(1 << lev) > scale) ++lev;
+    int m = 1 << lev;
+    double acc = 0.0;
+    for (int p = 0; p < m; ++p)
+      for (int q = 0; p + q < m; ++q) {
+        double a0[3] = {1.0 - (double)(p + q) / m, (double)p / m, (double)q / m};
+        double a1[3] = {1.0 - (double)(p + q + 1) / m, (double)(p + 1) / m, (double)q / m};
+        double a2[3] = {1.0 - (double)(p + q + 1) / m, (double)p / m, (double)(q + 1) / m};
+        acc += rhs_subtri(G, Flo, Fhi, kind, prm, a0, a1, a2);
+        if (p + q + 2 <= m) {
+          double c0[3] = {1.0 - (double)(p + q + 2) / m, (double)(p + 1) / m, (double)(q + 1) / m};
+          acc += rhs_subtri(G, Flo, Fhi, kind, prm, a1, c0, a2);
+        }
+      }
+    // each sub-triangle has area |K| / m^2; Duffy Jacobian 2 |sub| u
+    b[i + n_tet * (int64_t)r] = 2.0 * G.area / ((double)m * m) * acc;
+  }
+}
+
+bem_status op_rhs(const bem_operator* op, int kind, int nrhs, const double* d_params, double* d_b, cudaStream_t s) {
+  const bem_mesh* m = op->mesh;
+  k_rhs<<<(unsigned)((m->n_tet + 127) / 128), 128, 0, s>>>(m->n_tet, m->d_tet, m->d_surf, m->d_col, kind, nrhs,
+                                                           d_params, d_b);
+  STBEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel-level inner potentials for arbitrary (point, panel) pairs
+// ---------------------------------------------------------------------------
+template <bool FP32>
+__global__ void k_inner(int64_t n, const double* x4, const double* tv, const int32_t* sv, int n_theta, double* out) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double* X = tv + 16 * k;
+  const int32_t* s = sv + 4 * k;
+  // corners: distinct spatial ids ascending; lower / upper times per corner
+  int ids[3], nid = 0;
+  for (int v = 0; v < 4; ++v) {
+    bool dup = false;
+    for (int q = 0; q < nid; ++q) dup |= ids[q] == s[v];
+    if (!dup && nid < 3) ids[nid++] = s[v];
+  }
+  if (nid != 3) { out[k] = nan(""); return; }
+  for (int a = 1; a < 3; ++a)
+    for (int b = a; b > 0 && ids[b - 1] > ids[b]; --b) { int t = ids[b]; ids[b] = ids[b - 1]; ids[b - 1] = t; }
+  double cx[3][3];
+  FaceGeom Flo, Fhi;
+  for (int c = 0; c < 3; ++c) {
+    double lo = 1e300, hi = -1e300;
+    for (int v = 0; v < 4; ++v)
+      if (s[v] == ids[c]) {
+        for (int i = 0; i < 3; ++i) cx[c][i] = X[4 * v + 1 + i];
+        lo = fmin(lo, X[4 * v]);
+        hi = fmax(hi, X[4 * v]);
+      }
+    Flo.p[c] = lo;
+    Fhi.p[c] = hi;
+  }
+  ColGeom G;
+  make_colgeom(cx[0], cx[1], cx[2], G);
+  face_gradient(G, Flo);
+  face_gradient(G, Fhi);
+  PointCol P;
+  point_col(x4 + 4 * k, G, P, FP32);
+  const ArcRule rule = make_rule(FP32 ? BEM_PREC_MIXED : BEM_PREC_FP64, n_theta);
+  double wl = face_W<FP32>(G, P, Flo, rule), wh = face_W<FP32>(G, P, Fhi, rule);
+  out[k] = (wl - wh) / (4.0 * STBEM_PI);
+}
+
+bem_status inner_potentials(int64_t n, const double* d_x4, const double* d_tets, const int32_t* d_sv, int prec,
+                            int n_theta, double* d_out, cudaStream_t s) {
+  if (n == 0) return BEM_OK;
+  unsigned g = (unsigned)((n + 127) / 128);
+  if (prec == BEM_PREC_MIXED) k_inner<true><<<g, 128, 0, s>>>(n, d_x4, d_tets, d_sv, n_theta, d_out);
+  else k_inner<false><<<g, 128, 0, s>>>(n, d_x4, d_tets, d_sv, n_theta, d_out);
+  STBEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Permutations between caller and internal panel order
+// ---------------------------------------------------------------------------
+__global__ void k_permute(const int32_t* perm, const double* in, double* out, int64_t n, int nrhs, int to_internal) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n * nrhs) return;
+  int64_t r = k / n, i = k % n;
+  int64_t p = perm[i];  // internal i -> caller p
+  if (to_internal) out[r * n + i] = in[r * n + p];
+  else out[r * n + p] = in[r * n + i];
+}
+
+bem_status permute(const int32_t* d_perm, const double* in, double* out, int64_t n, int nrhs, bool to_internal,
+                   cudaStream_t s) {
+  int64_t tot = n * nrhs;
+  if (tot == 0) return BEM_OK;
+  k_permute<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d_perm, in, out, n, nrhs, to_internal ? 1 : 0);
+  STBEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+}  // namespace stbem

@@ -1,0 +1,114 @@
+// Internal host-side structures of the library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/stbem.h"
+#include "stbem_quad.cuh"
+
+namespace stbem {
+
+void set_error(const std::string& msg);
+
+#define STBEM_CUDA(call)                                                                   \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      ::stbem::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));             \
+      return BEM_ERR_CUDA;                                                                 \
+    }                                                                                      \
+  } while (0)
+
+constexpr int MAX_COL_TETS = 192;   // panels sharing one spatial triangle
+constexpr int MAX_COL_SURF = 193;   // nu_t != 0 faces over one spatial triangle
+constexpr int MAX_NQ = 64;          // m_Q^2 outer points per face
+
+// Per panel data on the device (internal panel order: by column, then time).
+struct TetDev {
+  int32_t lo, hi;      // global surface ids of the lower / upper face
+  int32_t col;         // column (spatial triangle)
+  int32_t dup;         // corner index (0..2) of the vertical edge
+  double tmin, tmax;   // min / max vertex time
+  double pmax;         // running max of tmax within the column (window search)
+  double vt[4];        // vertex times: corner 0,1,2 lower times, then the upper time at `dup`
+  double ball[5];      // 4D ball of the vertices in input order: centre (t,x,y,z), radius
+};
+
+struct SurfDev {
+  int32_t col;
+  int32_t pad;
+  FaceGeom f;          // corner times and in-frame gradient
+};
+
+}  // namespace stbem
+
+struct bem_context {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  double sm_count = 0;
+};
+
+struct bem_mesh {
+  bem_context* ctx = nullptr;
+  int64_t n_tet = 0, n_col = 0, n_surf = 0;
+  int max_col_tets = 0, max_col_surf = 0;
+  std::vector<int32_t> perm;    // internal -> caller panel id
+  std::vector<int32_t> iperm;   // caller -> internal
+  std::vector<int32_t> col_tet_begin, col_surf_begin;  // [n_col+1]
+  double coord_scale = 1.0;     // max |coordinate| over all vertices (FP32 filter margins)
+  // device
+  stbem::ColGeom* d_col = nullptr;
+  int32_t* d_col_tet_begin = nullptr;
+  int32_t* d_col_surf_begin = nullptr;
+  stbem::SurfDev* d_surf = nullptr;
+  stbem::TetDev* d_tet = nullptr;
+  int32_t* d_perm = nullptr;    // internal -> caller
+};
+
+struct bem_operator {
+  bem_context* ctx = nullptr;
+  const bem_mesh* mesh = nullptr;
+  bem_op_opts opts{};
+  int mq = 3, nq = 9, n_theta = 12;
+  double* d_pts = nullptr;       // [n_surf][nq][4] outer points
+  double* d_pts_trange = nullptr;// [n_surf][2] min / max time of the outer points
+  int32_t* d_bw = nullptr;       // [n_col*n_col] band width per column block
+  int64_t* d_bnnz = nullptr;     // [n_col*n_col] pattern entries per block
+  int64_t* d_boff = nullptr;     // [n_col*n_col] value offset
+  int64_t* d_rsoff = nullptr;    // [n_col*n_col] row-start offset
+  int32_t* d_rs = nullptr;       // row starts (internal trial index)
+  double* d_val = nullptr;       // values, per block column-major [W][R_I]
+  float* d_val32 = nullptr;
+  int64_t nnz = 0, nstored = 0, nblocks = 0, nrows_stored = 0;
+  double assemble_ms = 0.0;
+  double phase_ms[4] = {0, 0, 0, 0};
+  unsigned long long* d_counter = nullptr;  // work counter of the persistent kernels
+  // quadrature scratch
+  double* d_tmp = nullptr;
+  int64_t tmp_len = 0;
+};
+
+namespace stbem {
+// kernels wrappers (stbem_core.cu)
+bem_status upload_gauss_tables();
+bem_status mesh_device_geometry(bem_mesh* m, const double* d_sv_xyz, const int32_t* d_col_corner_sv,
+                                const double* d_tet_vx, const int32_t* d_tet_info, const double* d_surf_p);
+bem_status op_outer_points(bem_operator* op, cudaStream_t s);
+bem_status op_pattern(bem_operator* op, cudaStream_t s);
+bem_status op_quadrature(bem_operator* op, cudaStream_t s);
+bem_status op_matvec(const bem_operator* op, const double* x, double* y, int nrhs, bool fp32, cudaStream_t s);
+bem_status op_rhs(const bem_operator* op, int kind, int nrhs, const double* d_params, double* d_b, cudaStream_t s);
+bem_status op_entries(const bem_operator* op, int64_t n, const int32_t* d_ij, double* d_out, cudaStream_t s);
+bem_status op_pattern_csr(const bem_operator* op, int64_t* d_rowcount, int64_t* d_rowptr, int32_t* d_cols,
+                          bool fill, cudaStream_t s);
+bem_status inner_potentials(int64_t n, const double* d_x4, const double* d_tets, const int32_t* d_sv, int prec,
+                            int n_theta, double* d_out, cudaStream_t s);
+bem_status permute(const int32_t* d_perm, const double* in, double* out, int64_t n, int nrhs, bool to_internal,
+                   cudaStream_t s);
+// solver (stbem_solver.cu)
+bem_status gmres_solve(bem_operator* op, const double* d_b, double* d_x, int nrhs, const bem_solve_opts* o,
+                       bem_solve_info* info, cudaStream_t s);
+}  // namespace stbem

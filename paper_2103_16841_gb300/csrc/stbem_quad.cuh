@@ -1,0 +1,764 @@
+// Device math of the light-cone-clipped single-layer quadrature.
+//
+// For an apex x = (t, x_s) and a flat spatial triangle K, the retarded single
+// layer potential (eq. slp) of a panel sigma that lies between the graphs
+// tau = P_lo(y) and tau = P_hi(y) over K is, after the delta is integrated
+// over tau on the panel hyperplane Gamma_K x R,
+//
+//     V 1_sigma (x) = W_{P_lo}(x) - W_{P_hi}(x),
+//     W_P(x) = 1/(4 pi) int_K 1[P(y) + |x_s - y| < t] / |x_s - y| dA(y).
+//
+// W_P is the potential of the half-infinite column above the face tau = P(y);
+// its lit set R = K cap E, E = {y : P(y) + |x_s - y| < t}, is convex. In polar
+// coordinates (r = |x_s - y|, phi) around the foot point xb of x_s,
+// dA / r = dr dphi (the regularisation that the Lemma kernel_para expresses
+// as k_{psi,1} J = r0 on the chart l_2), so by Green's theorem, with the
+// winding number oint dphi = 2 pi 1[xb in R] folded in,
+//
+//     4 pi W_P = oint_{dR} (r - |d|) dphi,
+//
+// d the signed height of x_s over the plane of K. The boundary of R consists
+// of pieces of the triangle edges (closed form below) and arcs of the conic
+// dE (the light cone cut by the face plane). The conic arcs are integrated on
+// the circle of cone directions n(theta) that hit the face plane,
+// <n, c n_K + d grad P> = d, where the integrand (r - |d|) dphi/dtheta is a
+// rational trigonometric function; the Gauss-Legendre order follows from its
+// nearest pole, and near poles get a sinh map (Johnston & Elliott 2005).
+// For d = 0 the conic has its focus at xb and the arc integral is closed form.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#ifndef STBEM_PI
+#define STBEM_PI 3.14159265358979323846
+#endif
+
+namespace stbem {
+
+constexpr int MAX_NTHETA = 32;
+
+// Gauss-Legendre nodes/weights on [-1,1] for n = 1..MAX_NTHETA, packed:
+// rule n starts at offset n*(n-1)/2 (filled by upload_gauss_tables in the
+// translation unit that launches the quadrature kernels).
+static __constant__ double c_gl_x[MAX_NTHETA * (MAX_NTHETA + 1) / 2];
+static __constant__ double c_gl_w[MAX_NTHETA * (MAX_NTHETA + 1) / 2];
+// host copies (the same functions also compile for the host, for checks)
+static double h_gl_x[MAX_NTHETA * (MAX_NTHETA + 1) / 2];
+static double h_gl_w[MAX_NTHETA * (MAX_NTHETA + 1) / 2];
+
+#define STBEM_HD __host__ __device__
+
+STBEM_HD inline const double* gl_x() {
+#ifdef __CUDA_ARCH__
+  return c_gl_x;
+#else
+  return h_gl_x;
+#endif
+}
+STBEM_HD inline const double* gl_w() {
+#ifdef __CUDA_ARCH__
+  return c_gl_w;
+#else
+  return h_gl_w;
+#endif
+}
+
+struct ColGeom {         // per spatial triangle ("column"), column frame
+  double X[3][3];        // corners (input coordinates), ascending spatial-vertex id
+  double c0[3];          // corner 0
+  double e1[3], e2[3], n[3];
+  double Q[3][2];        // corners in the frame (Q[0] = 0); counter-clockwise
+  double U[3][2];        // unit edge directions, edge k: Q[k] -> Q[k+1]
+  double L[3];           // edge lengths
+  double area, diam;
+  double ctr[3], rad;    // centroid ball (pruning only)
+};
+
+struct FaceGeom {
+  double p[3];   // face times at the three corners
+  double g[2];   // gradient of P in the column frame
+};
+
+template <typename R>
+struct PtR {             // apex-against-column quantities in precision R (column frame)
+  R d;                   // signed height over the plane of K (0 if |d| < 1e-13 diam)
+  R xb[2];               // foot point
+  R q[3][2];             // corners relative to xb
+  R ps[3];               // signed distance of xb to edge line k (> 0 inside)
+  R ws[3];               // coordinate of Q[k] along edge k, origin at the foot of xb
+  R rs[3];               // |x_s - corner_k| in precision R
+  R Efull[3];            // int (r - |d|) dphi along the whole edge k
+};
+
+struct PointCol {        // apex x against one column
+  double t;
+  double r[3];           // |x_s - corner_k| (FP64: the cone-function values need it)
+  double rlo;            // lower bound of dist(x_s, K)
+  double Wst;            // 4 pi * potential of the whole triangle
+  int inK;
+  PtR<double> D;
+  PtR<float> F;          // filled for the mixed-precision path
+  float rho_hi[3], rho_lo[3];   // r_k - t as an FP32 pair (mixed path)
+  float nt_hi, nt_lo;           // -t as an FP32 pair
+  float rlot_hi, rlot_lo;       // rlo - t as an FP32 pair
+};
+
+// per face, FP32 view for the mixed path: corner times as FP32 pairs
+struct FaceF {
+  float p_hi[3], p_lo[3];
+  float g[2];
+  float pmin_hi, pmin_lo;
+};
+
+STBEM_HD inline void split2(double v, float& hi, float& lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+
+// a + b for FP32 pairs (TwoSum on the high parts), rounded to one float
+STBEM_HD inline float add2(float ahi, float alo, float bhi, float blo) {
+  float s = ahi + bhi;
+  float bb = s - ahi;
+  float e = (ahi - (s - bb)) + (bhi - bb);
+  return s + (e + (alo + blo));
+}
+
+STBEM_HD inline void make_facef(const FaceGeom& F, FaceF& o) {
+  int km = 0;
+  for (int k = 0; k < 3; ++k) {
+    split2(F.p[k], o.p_hi[k], o.p_lo[k]);
+    if (F.p[k] < F.p[km]) km = k;
+  }
+  o.pmin_hi = o.p_hi[km]; o.pmin_lo = o.p_lo[km];
+  o.g[0] = (float)F.g[0]; o.g[1] = (float)F.g[1];
+}
+
+template <typename R>
+struct ColR {            // edge data of a column in precision R
+  R U[3][2], L[3], diam;
+};
+
+STBEM_HD inline void sc(float x, float* s, float* c) { sincosf(x, s, c); }
+STBEM_HD inline void sc(double x, double* s, double* c) { sincos(x, s, c); }
+
+template <typename R>
+STBEM_HD inline const PtR<R>& pt(const PointCol& P);
+template <>
+STBEM_HD inline const PtR<double>& pt<double>(const PointCol& P) { return P.D; }
+template <>
+STBEM_HD inline const PtR<float>& pt<float>(const PointCol& P) { return P.F; }
+
+// ---------------------------------------------------------------------------
+// Green's theorem with the winding number removed: since oint dphi equals
+// 2 pi 1[xb in R],  4 pi W = oint_{dR} (r - |d|) dphi.
+// Along the line of edge k (signed distance p_s of xb, edge coordinate w
+// with the foot of the perpendicular at 0, r = sqrt(A^2 + w^2),
+// A^2 = p_s^2 + d^2):  (r - |d|) dphi = (r - |d|) p_s / (p^2 + w^2) dw, with
+// antiderivative
+//   E(w) = p_s asinh(w / A) - sgn(p_s) |d| atan(w p (p^2 + w^2) / ((r + |d|)(p^2 r + w^2 |d|)))
+// (the atan is the difference of atan(w |d| / (p r)) and the plain angle
+// atan(w / p)). Differences E(w_b) - E(w_a) are formed without cancellation:
+// asinh(w_b/A) - asinh(w_a/A) = asinh((w_b r_a - w_a r_b) / A^2) and
+// w_b r_a - w_a r_b = A^2 (w_b - w_a)(w_b + w_a) / (w_b r_a + w_a r_b) when
+// w_a w_b >= 0.
+// ---------------------------------------------------------------------------
+template <typename R>
+STBEM_HD inline R edge_T(R w, R r, R p, R ad) {
+  return atan(w * p * (p * p + w * w) / ((r + ad) * (p * p * r + w * w * ad)));
+}
+
+template <typename R>
+STBEM_HD inline R edge_dE(R wa, R wb, R p_s, R d) {
+  R p = fabs(p_s), ad = fabs(d);
+  R A2 = p_s * p_s + d * d;
+  if (A2 == R(0) || wa == wb) return R(0);
+  R ra = sqrt(A2 + wa * wa), rb = sqrt(A2 + wb * wb);
+  R dasinh;
+  if (wa * wb >= R(0)) dasinh = asinh((wb - wa) * (wb + wa) / (wb * ra + wa * rb));
+  else dasinh = asinh((wb * ra - wa * rb) / A2);
+  R val = p_s * dasinh;
+  if (p > R(0) && ad > R(0)) {
+    R dt = edge_T<R>(wb, rb, p, ad) - edge_T<R>(wa, ra, p, ad);
+    val -= (p_s > R(0) ? ad : -ad) * dt;
+  }
+  return val;
+}
+
+template <typename R>
+STBEM_HD inline void fill_pt(PtR<R>& T, const PtR<double>& D, const ColGeom& G, const double* r) {
+  T.d = (R)D.d;
+  for (int k = 0; k < 2; ++k) T.xb[k] = (R)D.xb[k];
+  for (int k = 0; k < 3; ++k) {
+    T.q[k][0] = (R)D.q[k][0]; T.q[k][1] = (R)D.q[k][1];
+    T.ps[k] = (R)D.ps[k]; T.ws[k] = (R)D.ws[k]; T.rs[k] = (R)r[k];
+    T.Efull[k] = edge_dE<R>(T.ws[k], (R)(D.ws[k] + G.L[k]), T.ps[k], T.d);
+  }
+}
+
+// Geometry of apex x against column G (FP64) and the whole-triangle
+// potential (the fully lit case), in FP64 or (prec_fp32) with FP32 closed forms.
+STBEM_HD inline void point_col(const double* x, const ColGeom& G, PointCol& P, bool prec_fp32) {
+  P.t = x[0];
+  double rel[3] = {x[1] - G.c0[0], x[2] - G.c0[1], x[3] - G.c0[2]};
+  double d = rel[0] * G.n[0] + rel[1] * G.n[1] + rel[2] * G.n[2];
+  if (fabs(d) < 1e-13 * G.diam) d = 0.0;
+  PtR<double>& D = P.D;
+  D.d = d;
+  D.xb[0] = rel[0] * G.e1[0] + rel[1] * G.e1[1] + rel[2] * G.e1[2];
+  D.xb[1] = rel[0] * G.e2[0] + rel[1] * G.e2[1] + rel[2] * G.e2[2];
+  int in = 1;
+  double out = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    D.q[k][0] = G.Q[k][0] - D.xb[0];
+    D.q[k][1] = G.Q[k][1] - D.xb[1];
+    double dx = x[1] - G.X[k][0], dy = x[2] - G.X[k][1], dz = x[3] - G.X[k][2];
+    P.r[k] = sqrt(dx * dx + dy * dy + dz * dz);
+  }
+  for (int k = 0; k < 3; ++k) {
+    D.ps[k] = D.q[k][0] * G.U[k][1] - D.q[k][1] * G.U[k][0];
+    D.ws[k] = D.q[k][0] * G.U[k][0] + D.q[k][1] * G.U[k][1];
+    D.rs[k] = P.r[k];
+    if (!(D.ps[k] > 0.0)) in = 0;
+    out = fmax(out, -D.ps[k]);
+  }
+  P.inK = in;
+  P.rlo = sqrt(d * d + out * out);
+  double W = 0.0;
+  if (prec_fp32) {
+    fill_pt<float>(P.F, D, G, P.r);
+    for (int k = 0; k < 3; ++k) {
+      W += (double)P.F.Efull[k];
+      split2(P.r[k] - P.t, P.rho_hi[k], P.rho_lo[k]);
+    }
+    split2(-P.t, P.nt_hi, P.nt_lo);
+    split2(P.rlo - P.t, P.rlot_hi, P.rlot_lo);
+  } else {
+    for (int k = 0; k < 3; ++k) {
+      D.Efull[k] = edge_dE<double>(D.ws[k], D.ws[k] + G.L[k], D.ps[k], d);
+      W += D.Efull[k];
+    }
+  }
+  P.Wst = W;
+}
+
+// ---------------------------------------------------------------------------
+// Conic arcs (all in precision R)
+// ---------------------------------------------------------------------------
+template <typename R>
+struct ArcFrame {
+  R wh[3], ea[3], eb[3];  // circle of directions: n = ca wh + sa (cos th ea + sin th eb)
+  R ca, sa;
+  R c, d, g[2];
+};
+
+template <typename R>
+STBEM_HD inline bool arc_frame(R c, R d, const R* g, ArcFrame<R>& F) {
+  R w[3] = {d * g[0], d * g[1], c};
+  R wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  if (!(wn > R(0))) return false;
+  R D0 = c * c - d * d * (R(1) - (g[0] * g[0] + g[1] * g[1]));
+  if (!(D0 > R(0))) return false;
+  for (int i = 0; i < 3; ++i) F.wh[i] = w[i] / wn;
+  F.ca = d / wn;
+  F.sa = sqrt(D0) / wn;
+  R a[3] = {R(1), R(0), R(0)};
+  if (fabs(F.wh[0]) >= R(0.8)) { a[0] = R(0); a[1] = R(1); }
+  R pa = a[0] * F.wh[0] + a[1] * F.wh[1] + a[2] * F.wh[2];
+  R ea[3] = {a[0] - pa * F.wh[0], a[1] - pa * F.wh[1], a[2] - pa * F.wh[2]};
+  R la = sqrt(ea[0] * ea[0] + ea[1] * ea[1] + ea[2] * ea[2]);
+  for (int i = 0; i < 3; ++i) F.ea[i] = ea[i] / la;
+  F.eb[0] = F.wh[1] * F.ea[2] - F.wh[2] * F.ea[1];
+  F.eb[1] = F.wh[2] * F.ea[0] - F.wh[0] * F.ea[2];
+  F.eb[2] = F.wh[0] * F.ea[1] - F.wh[1] * F.ea[0];
+  F.c = c; F.d = d; F.g[0] = g[0]; F.g[1] = g[1];
+  return true;
+}
+
+template <typename R>
+STBEM_HD inline R arc_theta(const ArcFrame<R>& F, const R* y) {
+  R r = sqrt(y[0] * y[0] + y[1] * y[1] + F.d * F.d);
+  R nh[3] = {-y[0] / r, -y[1] / r, F.d / r};
+  R cb = nh[0] * F.eb[0] + nh[1] * F.eb[1] + nh[2] * F.eb[2];
+  R cA = nh[0] * F.ea[0] + nh[1] * F.ea[1] + nh[2] * F.ea[2];
+  return atan2(cb, cA);
+}
+
+// direction of the conic point y(theta) = -r n_par; returns r, n_par, n_par', n_n, n_n'
+template <typename R>
+STBEM_HD inline void arc_point(const ArcFrame<R>& F, R th, R& r, R* np, R* dp, R& nn, R& dn) {
+  R s, co;
+  sc(th, &s, &co);
+  R n3[3], d3[3];
+  for (int i = 0; i < 3; ++i) {
+    n3[i] = F.ca * F.wh[i] + F.sa * (co * F.ea[i] + s * F.eb[i]);
+    d3[i] = F.sa * (-s * F.ea[i] + co * F.eb[i]);
+  }
+  np[0] = n3[0]; np[1] = n3[1]; dp[0] = d3[0]; dp[1] = d3[1]; nn = n3[2]; dn = d3[2];
+  if (fabs(F.c) >= fabs(F.d)) r = F.c / (R(1) - (F.g[0] * np[0] + F.g[1] * np[1]));
+  else r = F.d / nn;
+}
+
+// Arc integrand of (r - |d|) dphi: with r - |d| = r^2 |n_par|^2 / (r + |d|) and
+// dphi/dth = cross(n_par, n_par') / |n_par|^2,
+//   I(th) = r(th)^2 cross(n_par, n_par') / (r(th) + |d|),
+// the direction basis rotated so that th is measured from the interval midpoint.
+template <typename R>
+struct ArcEval {
+  R ca, sa;
+  R wh[3], ea[3], eb[3];
+  R c, d, g0, g1;
+  bool use_c;
+  STBEM_HD inline R operator()(R th) const {
+    R s, co;
+    sc(th, &s, &co);
+    R n0 = ca * wh[0] + sa * (co * ea[0] + s * eb[0]);
+    R n1 = ca * wh[1] + sa * (co * ea[1] + s * eb[1]);
+    R n2 = ca * wh[2] + sa * (co * ea[2] + s * eb[2]);
+    R d0 = sa * (-s * ea[0] + co * eb[0]);
+    R d1 = sa * (-s * ea[1] + co * eb[1]);
+    R r = use_c ? c / (R(1) - (g0 * n0 + g1 * n1)) : d / n2;
+    R cr = n0 * d1 - n1 * d0;
+    return r * r * cr / (r + fabs(d));
+  }
+};
+
+// Nearest pole of A0 - A1 cos(theta - th1), in the coordinate u of the
+// interval [mid - half, mid + half] -> [-1, 1]: keeps the pole with the
+// smallest Bernstein-ellipse parameter rho = s + sqrt(s^2 - 1),
+// s = (|u - 1| + |u + 1|) / 2. Complex zeros th1 +- i acosh(A0/A1) when
+// A0 > A1; real zeros th1 +- acos(A0/A1) otherwise (the asymptote directions
+// of a hyperbolic conic: outside the arc, but possibly close to its ends).
+template <typename R>
+STBEM_HD inline void pole_at(R th, R eta, R mid, R half, R& best_rho, R& best_a, R& best_b) {
+  const R twopi = (R)(2.0 * STBEM_PI);
+  R k = rint((mid - th) / twopi);
+  R a = (th + twopi * k - mid) / half;
+  R b = eta / half;
+  R s = R(0.5) * (sqrt((a - R(1)) * (a - R(1)) + b * b) + sqrt((a + R(1)) * (a + R(1)) + b * b));
+  R rho = s + sqrt(fmax(s * s - R(1), R(0)));
+  if (rho < best_rho) { best_rho = rho; best_a = a; best_b = b; }
+}
+template <typename R>
+STBEM_HD inline void consider_pole(R A0, R Aa, R Ab, R mid, R half, R& best_rho, R& best_a, R& best_b) {
+  R A1 = sqrt(Aa * Aa + Ab * Ab);
+  if (!(A1 > R(0))) return;
+  R th1 = atan2(Ab, Aa);
+  if (A0 > A1) {
+    pole_at<R>(th1, acosh(A0 / A1), mid, half, best_rho, best_a, best_b);
+  } else {
+    R ac = acos(fmax(R(-1), A0 / A1));
+    pole_at<R>(th1 + ac, R(0), mid, half, best_rho, best_a, best_b);
+    pole_at<R>(th1 - ac, R(0), mid, half, best_rho, best_a, best_b);
+  }
+}
+
+struct ArcRule {
+  int nmin, nmax;    // Gauss node bounds per piece
+  double tol;        // target relative accuracy of a piece
+};
+
+// n_max = 0 selects the default cap (32 nodes FP64, 16 nodes MIXED).
+STBEM_HD inline ArcRule make_rule(int precision_mixed, int n_max) {
+  ArcRule r;
+  if (precision_mixed) { r.nmin = 4; r.nmax = n_max ? n_max : 16; r.tol = 1e-7; }
+  else { r.nmin = 6; r.nmax = n_max ? n_max : 32; r.tol = 1e-15; }
+  if (r.nmin > r.nmax) r.nmin = r.nmax;
+  return r;
+}
+
+// int_lo^hi I(theta) dtheta. The integrand is a rational trigonometric
+// function; its nearest pole sets the Gauss-Legendre order needed
+// (error ~ rho^(-2n)). Poles closer than 0.3 half-lengths to the interval
+// get a sinh map towards them (Johnston & Elliott 2005) instead.
+template <typename R>
+STBEM_HD __noinline__ R arc_piece(const ArcFrame<R>& F, R lo, R hi, const ArcRule& rule) {
+  R mid = R(0.5) * (lo + hi), half = R(0.5) * (hi - lo);
+  R best_rho = R(1e30), best_a = R(0), best_b = R(1e30);
+  {
+    // poles of I: L1 = 1 - <g, n_par> = 0 (r -> infinity) and
+    // r + |d| = 0, i.e. L1 = -c / |d| (complex for the valid arc)
+    R gw = F.g[0] * F.wh[0] + F.g[1] * F.wh[1];
+    R ga = F.g[0] * F.ea[0] + F.g[1] * F.ea[1];
+    R gb = F.g[0] * F.eb[0] + F.g[1] * F.eb[1];
+    consider_pole<R>(R(1) - F.ca * gw, F.sa * ga, F.sa * gb, mid, half, best_rho, best_a, best_b);
+    consider_pole<R>(R(1) + F.c / fabs(F.d) - F.ca * gw, F.sa * ga, F.sa * gb, mid, half, best_rho, best_a, best_b);
+  }
+  R sm, cm;
+  sc(mid, &sm, &cm);
+  ArcEval<R> E;
+  E.ca = F.ca; E.sa = F.sa;
+  for (int i = 0; i < 3; ++i) {
+    E.wh[i] = F.wh[i];
+    E.ea[i] = cm * F.ea[i] + sm * F.eb[i];
+    E.eb[i] = -sm * F.ea[i] + cm * F.eb[i];
+  }
+  E.c = F.c; E.d = F.d; E.g0 = F.g[0]; E.g1 = F.g[1];
+  E.use_c = fabs(F.c) >= fabs(F.d);
+  R acc = R(0);
+  if (best_b < R(0.3)) {
+    const int n = rule.nmax;
+    const double* X = gl_x() + n * (n - 1) / 2;
+    const double* Wt = gl_w() + n * (n - 1) / 2;
+    R a = best_a, b = best_b;
+    if (a > R(1)) { b = sqrt((a - R(1)) * (a - R(1)) + b * b); a = R(1); }
+    else if (a < R(-1)) { b = sqrt((a + R(1)) * (a + R(1)) + b * b); a = R(-1); }
+    R s1 = asinh((R(1) + a) / b), s2 = asinh((R(1) - a) / b);
+    R mu = R(0.5) * (s1 + s2), et = R(0.5) * (s1 - s2);
+    for (int k = 0; k < n; ++k) {
+      R v = mu * (R)X[k] - et;
+      R u = a + b * sinh(v);
+      acc += (R)Wt[k] * b * mu * cosh(v) * E(half * u);
+    }
+  } else {
+    int n = rule.nmin;
+    if (best_rho < R(1e29)) {
+      int need = (int)ceil(log(R(1.0 / rule.tol)) / (R(2) * log(best_rho))) + 1;
+      n = need < rule.nmin ? rule.nmin : (need > rule.nmax ? rule.nmax : need);
+    }
+    const double* X = gl_x() + n * (n - 1) / 2;
+    const double* Wt = gl_w() + n * (n - 1) / 2;
+    for (int k = 0; k < n; ++k) acc += (R)Wt[k] * E(half * (R)X[k]);
+  }
+  return acc * half;
+}
+
+// d = 0: the conic r = c / (1 + G0 cos(psi)), psi = phi - phi_g, has its
+// focus at xb; exact antiderivatives of dpsi / (1 + e cos psi).
+template <typename R>
+STBEM_HD inline R arc_d0_U(R psi, R e) {
+  const R pi = (R)STBEM_PI;
+  if (e < R(1)) {
+    R k = sqrt((R(1) - e) / (R(1) + e));
+    return R(2) / sqrt(R(1) - e * e) * (atan(k * tan(R(0.5) * psi)) + pi * floor((psi + pi) / (R(2) * pi)));
+  } else if (e > R(1)) {
+    // ln|(a + b tan(psi/2)) / (a - b tan(psi/2))| / sqrt(e^2-1), a = sqrt(e+1), b = sqrt(e-1):
+    // continuous through psi = pi, singular only on the asymptote directions
+    R a = sqrt(e + R(1)), b = sqrt(e - R(1));
+    R s, co;
+    sc(R(0.5) * psi, &s, &co);
+    return log(fabs((a * co + b * s) / (a * co - b * s))) / sqrt(e * e - R(1));
+  }
+  return tan(R(0.5) * psi);
+}
+
+template <typename R>
+STBEM_HD inline R arc_d0(const R* A, const R* B, bool full, R c, const R* g) {
+  if (c == R(0)) return R(0);
+  const R pi = (R)STBEM_PI, twopi = (R)(2.0 * STBEM_PI);
+  R G0 = sqrt(g[0] * g[0] + g[1] * g[1]);
+  if (full) return twopi * c / sqrt(R(1) - G0 * G0);
+  R phg = G0 > R(0) ? atan2(g[1], g[0]) : R(0);
+  R pa = atan2(A[1], A[0]), pb = atan2(B[1], B[0]);
+  R span;
+  if (c > R(0)) { span = fmod(pb - pa, twopi); if (span < R(0)) span += twopi; }
+  else { span = fmod(pa - pb, twopi); if (span < R(0)) span += twopi; span = -span; }
+  R psa = pa - phg;
+  psa = fmod(psa + pi, twopi);
+  if (psa < R(0)) psa += twopi;
+  psa -= pi;
+  return c * (arc_d0_U<R>(psa + span, G0) - arc_d0_U<R>(psa, G0));
+}
+
+// Arc from point A to point B (relative to xb) along dE with E on the left;
+// full = closed ellipse (A, B ignored).
+template <typename R>
+STBEM_HD __noinline__ R conic_arc(const R* A, const R* B, bool full, R c, R d, const R* g, const ArcRule& rule,
+                                  double c64, const double* g64) {
+  if (d == R(0)) {
+    // closed form in FP64 in every precision: it is a difference of
+    // antiderivative values, and it only arises for coplanar pairs
+    double A64[2] = {A ? (double)A[0] : 0.0, A ? (double)A[1] : 0.0};
+    double B64[2] = {B ? (double)B[0] : 0.0, B ? (double)B[1] : 0.0};
+    return (R)arc_d0<double>(A64, B64, full, c64, g64);
+  }
+  ArcFrame<R> F;
+  if (!arc_frame<R>(c, d, g, F)) return R(0);
+  if (F.sa < R(sizeof(R) == 4 ? 1e-6 : 1e-14)) return R(0);
+  const R pi = (R)STBEM_PI, twopi = (R)(2.0 * STBEM_PI);
+  R thA = full ? R(0) : arc_theta<R>(F, A);
+  // orientation: tangent dy/dtheta against grad F = g + y/r at the start point
+  R r, np[2], dp[2], nn, dn;
+  arc_point<R>(F, thA, r, np, dp, nn, dn);
+  R dr;
+  if (fabs(F.c) >= fabs(F.d)) {
+    R L1 = R(1) - (g[0] * np[0] + g[1] * np[1]);
+    dr = r * (g[0] * dp[0] + g[1] * dp[1]) / L1;
+  } else {
+    dr = -r * dn / nn;
+  }
+  R T[2] = {-dr * np[0] - r * dp[0], -dr * np[1] - r * dp[1]};
+  R y[2] = {-r * np[0], -r * np[1]};
+  R ry = sqrt(y[0] * y[0] + y[1] * y[1] + d * d);
+  R gF[2] = {g[0] + y[0] / ry, g[1] + y[1] / ry};
+  R s = (T[0] * gF[1] - T[1] * gF[0]) < R(0) ? R(1) : R(-1);
+  R span;
+  if (full) span = twopi;
+  else {
+    R thB = arc_theta<R>(F, B);
+    span = s > R(0) ? fmod(thB - thA, twopi) : fmod(thA - thB, twopi);
+    if (span < R(0)) span += twopi;
+  }
+  R lo = s > R(0) ? thA : thA - span;
+  R hi = s > R(0) ? thA + span : thA;
+  R val;
+  if (span > pi) {
+    R m = R(0.5) * (lo + hi);
+    val = arc_piece<R>(F, lo, m, rule) + arc_piece<R>(F, m, hi, rule);
+  } else {
+    val = arc_piece<R>(F, lo, hi, rule);
+  }
+  return s * val;
+}
+
+// Column frame of a spatial triangle with corners X0, X1, X2 (counter-clockwise
+// in the frame by construction: n = (X1-X0) x (X2-X0)).
+STBEM_HD inline void make_colgeom(const double* X0, const double* X1, const double* X2, ColGeom& G) {
+  for (int i = 0; i < 3; ++i) {
+    G.X[0][i] = X0[i]; G.X[1][i] = X1[i]; G.X[2][i] = X2[i];
+    G.c0[i] = X0[i];
+  }
+  double a[3] = {X1[0] - X0[0], X1[1] - X0[1], X1[2] - X0[2]};
+  double b[3] = {X2[0] - X0[0], X2[1] - X0[1], X2[2] - X0[2]};
+  double n[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+  double nl = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  double al = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+  for (int i = 0; i < 3; ++i) { G.n[i] = n[i] / nl; G.e1[i] = a[i] / al; }
+  G.e2[0] = G.n[1] * G.e1[2] - G.n[2] * G.e1[1];
+  G.e2[1] = G.n[2] * G.e1[0] - G.n[0] * G.e1[2];
+  G.e2[2] = G.n[0] * G.e1[1] - G.n[1] * G.e1[0];
+  G.Q[0][0] = 0.0; G.Q[0][1] = 0.0;
+  G.Q[1][0] = al;  G.Q[1][1] = 0.0;
+  G.Q[2][0] = b[0] * G.e1[0] + b[1] * G.e1[1] + b[2] * G.e1[2];
+  G.Q[2][1] = b[0] * G.e2[0] + b[1] * G.e2[1] + b[2] * G.e2[2];
+  G.diam = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    int k1 = (k + 1) % 3;
+    double ex = G.Q[k1][0] - G.Q[k][0], ey = G.Q[k1][1] - G.Q[k][1];
+    double l = sqrt(ex * ex + ey * ey);
+    G.L[k] = l; G.U[k][0] = ex / l; G.U[k][1] = ey / l;
+    G.diam = fmax(G.diam, l);
+  }
+  G.area = 0.5 * nl;
+  for (int i = 0; i < 3; ++i) G.ctr[i] = (X0[i] + X1[i] + X2[i]) / 3.0;
+  G.rad = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    double dx = G.X[k][0] - G.ctr[0], dy = G.X[k][1] - G.ctr[1], dz = G.X[k][2] - G.ctr[2];
+    G.rad = fmax(G.rad, sqrt(dx * dx + dy * dy + dz * dz));
+  }
+}
+
+STBEM_HD inline void face_gradient(const ColGeom& G, FaceGeom& F) {
+  F.g[0] = (F.p[1] - F.p[0]) / G.Q[1][0];
+  F.g[1] = ((F.p[2] - F.p[0]) - F.g[0] * G.Q[2][0]) / G.Q[2][1];
+}
+
+// ---------------------------------------------------------------------------
+// 4 pi W_P(x) for a face with corner times p[3] and in-frame gradient g.
+// Step 1 (FP64): cone-function values F_k = P(corner_k) + |x_s - corner_k| - t
+// at the corners decide the fully lit (all < 0: the whole-triangle value)
+// and certainly dark cases; c = t - P(xb).
+// Step 2 (precision R): the cut case, by Green's theorem on dR.
+// ---------------------------------------------------------------------------
+enum { FACE_DARK = 0, FACE_LIT = 1, FACE_CUT = 2 };
+
+STBEM_HD inline int face_class(const ColGeom& G, const PointCol& P, const FaceGeom& Fc, double* F, double& c) {
+  const double t = P.t;
+  int nlit = 0;
+  double pmin = Fc.p[0];
+  for (int k = 0; k < 3; ++k) {
+    F[k] = (Fc.p[k] - t) + P.r[k];
+    if (F[k] < 0.0) ++nlit;
+    pmin = fmin(pmin, Fc.p[k]);
+  }
+  if (nlit == 3) return FACE_LIT;
+  // P + r - t >= min p + dist(x_s, K) - t >= 0: no lit point
+  if ((pmin - t) + P.rlo >= 0.0) return FACE_DARK;
+  // c = t - P(xb), P(xb) = p0 + <g, xb - Q0>, Q0 = 0
+  c = t - (Fc.p[0] + Fc.g[0] * P.D.xb[0] + Fc.g[1] * P.D.xb[1]);
+  if (fabs(c) < 1e-13 * G.diam) c = 0.0;
+  return FACE_CUT;
+}
+
+// Step 1 for the mixed path in FP32 pairs: F_k = p_k + (r_k - t) and
+// c = -((p_0 - t) + <g, xb>) keep their absolute accuracy although p_k, r_k
+// and t are O(T) and F_k, c are O(diam K) near the cone.
+STBEM_HD inline int face_class_mixed(const PointCol& P, const FaceF& Fc, float* F, float& c, float diam) {
+  int nlit = 0;
+  for (int k = 0; k < 3; ++k) {
+    F[k] = add2(Fc.p_hi[k], Fc.p_lo[k], P.rho_hi[k], P.rho_lo[k]);
+    if (F[k] < 0.f) ++nlit;
+  }
+  if (nlit == 3) return FACE_LIT;
+  if (add2(Fc.pmin_hi, Fc.pmin_lo, P.rlot_hi, P.rlot_lo) >= 0.f) return FACE_DARK;
+  float p0t = add2(Fc.p_hi[0], Fc.p_lo[0], P.nt_hi, P.nt_lo);
+  c = -(p0t + (Fc.g[0] * P.F.xb[0] + Fc.g[1] * P.F.xb[1]));
+  if (fabsf(c) < 1e-6f * diam) c = 0.f;
+  return FACE_CUT;
+}
+
+// Inputs of the cut case in precision R: cone-function values F_k at the
+// corners, a0_k = t - p_k, a1_k = p_{k+1} - p_k, the in-frame gradient g,
+// c = t - P(xb); c64 / g64 feed the FP64 closed form of coplanar (d = 0) arcs.
+template <typename R>
+struct FaceCutIn {
+  R F[3], a0[3], a1[3], g[2], c;
+  double c64, g64[2];
+};
+
+STBEM_HD inline void cut_in_fp64(const PointCol& P, const FaceGeom& Fc, const double* F, double c,
+                                 FaceCutIn<double>& o) {
+  for (int k = 0; k < 3; ++k) {
+    o.F[k] = F[k];
+    o.a0[k] = P.t - Fc.p[k];
+    o.a1[k] = Fc.p[(k + 1) % 3] - Fc.p[k];
+  }
+  o.g[0] = o.g64[0] = Fc.g[0];
+  o.g[1] = o.g64[1] = Fc.g[1];
+  o.c = o.c64 = c;
+}
+
+STBEM_HD inline void cut_in_mixed(const PointCol& P, const FaceF& Fc, const float* F, float c, const FaceGeom& F64,
+                                  FaceCutIn<float>& o) {
+  for (int k = 0; k < 3; ++k) {
+    int k1 = (k + 1) % 3;
+    o.F[k] = F[k];
+    o.a0[k] = -add2(Fc.p_hi[k], Fc.p_lo[k], P.nt_hi, P.nt_lo);
+    o.a1[k] = add2(Fc.p_hi[k1], Fc.p_lo[k1], -Fc.p_hi[k], -Fc.p_lo[k]);
+  }
+  o.g[0] = Fc.g[0]; o.g[1] = Fc.g[1];
+  o.g64[0] = F64.g[0]; o.g64[1] = F64.g[1];
+  o.c = c;
+  o.c64 = (double)c;
+}
+
+template <typename R>
+STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, const FaceCutIn<R>& in,
+                                      const ArcRule& rule) {
+  const PtR<R>& P = pt<R>(P64);
+  const R d = P.d, c = in.c;
+  const R* g = in.g;
+  const R* F = in.F;
+  R total = R(0);
+  R ev_y[6][2];
+  int ev_in[6];
+  int nev = 0;
+  for (int k = 0; k < 3; ++k) {
+    int k1 = (k + 1) % 3;
+    R la = R(0), lb = R(1);
+    bool has = false, la_root = false, lb_root = false;
+    if (F[k] < R(0) && F[k1] < R(0)) {
+      has = true;
+    } else {
+      R a0 = in.a0[k], a1 = in.a1[k];
+      R Ex = G.U[k][0] * G.L[k], Ey = G.U[k][1] * G.L[k];
+      R A2 = G.L[k] * G.L[k] - a1 * a1;
+      R B2 = R(2) * ((P.q[k][0] * Ex + P.q[k][1] * Ey) + a0 * a1);
+      R C2 = F[k] * (P.rs[k] + a0);   // |q_k|^2 + d^2 - a0^2 without cancellation
+      R rt[2];
+      int nr = 0;
+      if (fabs(A2) <= R(sizeof(R) == 4 ? 1e-6 : 1e-14) * (G.L[k] * G.L[k] + a1 * a1)) {
+        if (B2 != R(0)) rt[nr++] = -C2 / B2;
+      } else {
+        R disc = B2 * B2 - R(4) * A2 * C2;
+        if (disc >= R(0)) {
+          R sq = sqrt(disc);
+          R qq = R(-0.5) * (B2 + (B2 >= R(0) ? sq : -sq));
+          if (qq != R(0)) { rt[nr++] = qq / A2; rt[nr++] = C2 / qq; }
+          else rt[nr++] = R(0);
+        }
+      }
+      // keep roots of r = a (a = t - P >= 0), not of r = -a
+      R v[2];
+      int nv = 0;
+      const R slack = R(sizeof(R) == 4 ? 1e-5 : 1e-12);
+      for (int i = 0; i < nr; ++i)
+        if (a0 - a1 * rt[i] > R(0) && rt[i] >= -slack && rt[i] <= R(1) + slack) v[nv++] = fmin(R(1), fmax(R(0), rt[i]));
+      if (nv == 2 && v[0] > v[1]) { R tmp = v[0]; v[0] = v[1]; v[1] = tmp; }
+      if (F[k] < R(0)) {           // exit on this edge
+        lb = nv ? v[0] : R(1); lb_root = nv > 0; has = true;
+      } else if (F[k1] < R(0)) {   // entry on this edge
+        la = nv ? v[nv - 1] : R(0); la_root = nv > 0; has = true;
+      } else if (nv == 2 && v[1] > v[0]) {
+        la = v[0]; lb = v[1]; la_root = lb_root = true; has = true;
+      }
+    }
+    if (!has) continue;
+    if (!la_root && !lb_root) total += P.Efull[k];
+    else total += edge_dE<R>(P.ws[k] + la * G.L[k], P.ws[k] + lb * G.L[k], P.ps[k], d);
+    if (la_root) {
+      ev_in[nev] = 1;
+      ev_y[nev][0] = P.q[k][0] + la * G.U[k][0] * G.L[k];
+      ev_y[nev][1] = P.q[k][1] + la * G.U[k][1] * G.L[k];
+      ++nev;
+    }
+    if (lb_root) {
+      ev_in[nev] = 0;
+      ev_y[nev][0] = P.q[k][0] + lb * G.U[k][0] * G.L[k];
+      ev_y[nev][1] = P.q[k][1] + lb * G.U[k][1] * G.L[k];
+      ++nev;
+    }
+  }
+  if (nev > 0) {
+    // events are in perimeter order; each exit connects to the next entry
+    for (int i = 0; i < nev; ++i) {
+      if (ev_in[i]) continue;
+      for (int s = 1; s <= nev; ++s) {
+        int j = (i + s) % nev;
+        if (ev_in[j]) { total += conic_arc<R>(ev_y[i], ev_y[j], false, c, d, g, rule, in.c64, in.g64); break; }
+      }
+    }
+  } else {
+    // no crossing: E inside K (closed ellipse) or E cap K empty
+    R G2 = g[0] * g[0] + g[1] * g[1];
+    if (!(G2 < R(1) && c > fabs(d) * sqrt(R(1) - G2))) return 0.0;
+    R G0 = sqrt(G2);
+    R sst = G0 > R(0) ? fabs(d) * G0 / sqrt(R(1) - G2) : R(0);
+    R yst[2] = {G0 > R(0) ? -sst * g[0] / G0 : R(0), G0 > R(0) ? -sst * g[1] / G0 : R(0)};
+    for (int k = 0; k < 3; ++k) {
+      R rel[2] = {yst[0] - P.q[k][0], yst[1] - P.q[k][1]};
+      if (!(G.U[k][0] * rel[1] - G.U[k][1] * rel[0] > R(0))) return 0.0;
+    }
+    total += conic_arc<R>(nullptr, nullptr, true, c, d, g, rule, in.c64, in.g64);
+  }
+  return (double)total;
+}
+
+template <typename R>
+STBEM_HD inline void make_colr(const ColGeom& G, ColR<R>& C) {
+  for (int k = 0; k < 3; ++k) {
+    C.U[k][0] = (R)G.U[k][0]; C.U[k][1] = (R)G.U[k][1]; C.L[k] = (R)G.L[k];
+  }
+  C.diam = (R)G.diam;
+}
+
+// 4 pi W_P(x) in one call (used by the kernel-level entry point and checks)
+template <bool FP32>
+STBEM_HD inline double face_W(const ColGeom& G, const PointCol& P, const FaceGeom& Fc, const ArcRule& rule) {
+  if (FP32) {
+    FaceF Ff;
+    make_facef(Fc, Ff);
+    float F[3], c = 0.f;
+    int cls = face_class_mixed(P, Ff, F, c, (float)G.diam);
+    if (cls == FACE_LIT) return P.Wst;
+    if (cls == FACE_DARK) return 0.0;
+    ColR<float> CR;
+    make_colr<float>(G, CR);
+    FaceCutIn<float> in;
+    cut_in_mixed(P, Ff, F, c, Fc, in);
+    return face_cut<float>(CR, P, in, rule);
+  }
+  double F[3], c = 0.0;
+  int cls = face_class(G, P, Fc, F, c);
+  if (cls == FACE_LIT) return P.Wst;
+  if (cls == FACE_DARK) return 0.0;
+  ColR<double> CR;
+  make_colr<double>(G, CR);
+  FaceCutIn<double> in;
+  cut_in_fp64(P, Fc, F, c, in);
+  return face_cut<double>(CR, P, in, rule);
+}
+
+}  // namespace stbem
