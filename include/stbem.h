@@ -124,7 +124,8 @@ typedef struct {
   int32_t n_theta;   /* cap on Gauss nodes per conic-arc piece (4..32); 0 = default (32 FP64, 16 MIXED).
                         The count per piece is chosen from the distance of the integrand's nearest
                         complex pole to reach 1e-15 (FP64) or 1e-7 (MIXED) relative accuracy. */
-  int32_t store_fp32;/* 1: also keep an FP32 copy of the values for low-precision matvecs */
+  int32_t store_fp32;/* FP64 operators: 1 also keeps an FP32 copy of the values for low-precision
+                        matvecs. MIXED operators always store FP32 values only (their accuracy). */
 } bem_op_opts;
 
 /* Assembles the sparse Galerkin matrix on the device.
@@ -136,7 +137,8 @@ typedef struct {
  * (Def. choice_r), the strong Huygens principle (the panel is not strictly
  * inside the cone) and the ball bound of Theorem phi_xi_sphere; entries
  * outside the pattern are exactly 0.0. The pattern decisions are made in
- * FP64 with the operation order of the published contract (bit-exact). */
+ * FP64 with the operation order of the published contract (bit-exact).
+ * Returns BEM_ERR_INTERNAL if any assembled value is not finite. */
 bem_status bem_operator_create(bem_context* ctx, const bem_mesh* mesh, const bem_op_opts* opts,
                                bem_operator** out);
 
@@ -145,6 +147,10 @@ bem_status bem_operator_create(bem_context* ctx, const bem_mesh* mesh, const bem
  * time of the last assembly. Any pointer may be NULL. */
 bem_status bem_operator_stats(const bem_operator* op, int64_t* nnz_pattern, int64_t* stored_values,
                               int64_t* n_blocks, double* assemble_ms);
+
+/* Scans the stored values on the device: number of non-finite values (NaN,
+ * Inf) and the largest magnitude. A healthy operator has n_nonfinite = 0. */
+bem_status bem_operator_check(const bem_operator* op, int64_t* n_nonfinite, double* max_abs);
 
 /* Device time of the last assembly by phase (CUDA events on the assembly
  * stream): ms[0] outer points, ms[1] sparsity pattern pass, ms[2] block
@@ -159,6 +165,13 @@ bem_status bem_operator_reassemble(bem_operator* op, void* stream);
 /* Pattern rows in the caller's numbering, CSR with ascending columns.
  * rowptr [n_tet+1] (int64), cols [nnz_pattern]. */
 bem_status bem_operator_export_pattern(const bem_operator* op, int64_t* rowptr, int32_t* cols);
+
+/* Pattern of selected rows (caller numbering): counts[k] = entries of row
+ * rows[k]; cols[k*cap ...] its first min(counts[k], cap) columns, ascending.
+ * Cost scales with the number of distinct spatial triangles of the rows, not
+ * with the mesh: meant for checks on large meshes. */
+bem_status bem_operator_pattern_rows(const bem_operator* op, int64_t n, const int32_t* rows, int64_t cap,
+                                     int64_t* counts, int32_t* cols);
 
 /* Dense matrix (row-major [n_tet][n_tet]); for small meshes (n_tet <= 20000). */
 bem_status bem_operator_export_dense(const bem_operator* op, double* A);

@@ -113,6 +113,13 @@ class Operator:
                                                   _lib.dptr(ms)))
         return {"nnz": int(a[0]), "stored": int(a[1]), "blocks": int(a[2]), "assemble_ms": float(ms[0])}
 
+    def check(self):
+        """(number of non-finite stored values, largest |value|)"""
+        n = np.zeros(1, dtype=np.int64)
+        mx = np.zeros(1)
+        _lib.check(self.ctx._L.bem_operator_check(self.h, _lib.lptr(n), _lib.dptr(mx)))
+        return int(n[0]), float(mx[0])
+
     def timings(self):
         ms = np.zeros(4)
         _lib.check(self.ctx._L.bem_operator_timings(self.h, _lib.dptr(ms)))
@@ -127,6 +134,16 @@ class Operator:
         cols = np.zeros(max(nnz, 1), dtype=np.int32)
         _lib.check(self.ctx._L.bem_operator_export_pattern(self.h, _lib.lptr(rowptr), _lib.iptr(cols)))
         return rowptr, cols[:nnz]
+
+    def pattern_rows(self, rows, cap=None):
+        """Admissible columns (ascending) of the listed rows."""
+        rows = np.ascontiguousarray(rows, dtype=np.int32)
+        cap = int(cap or self.n)
+        counts = np.zeros(rows.shape[0], dtype=np.int64)
+        cols = np.zeros(rows.shape[0] * cap, dtype=np.int32)
+        _lib.check(self.ctx._L.bem_operator_pattern_rows(self.h, rows.shape[0], _lib.iptr(rows), cap,
+                                                         _lib.lptr(counts), _lib.iptr(cols)))
+        return [cols[k * cap: k * cap + min(cap, counts[k])].copy() for k in range(rows.shape[0])]
 
     def export_dense(self):
         A = np.zeros((self.n, self.n))

@@ -26,7 +26,7 @@ DATA_PULSE = 1
 EXPORTS = [
     "bem_context_create", "bem_context_destroy", "bem_last_error", "bem_version",
     "bem_mesh_create", "bem_mesh_create_prisms", "bem_mesh_info", "bem_mesh_destroy",
-    "bem_operator_create", "bem_operator_stats", "bem_operator_timings", "bem_operator_reassemble", "bem_operator_export_pattern",
+    "bem_operator_create", "bem_operator_stats", "bem_operator_check", "bem_operator_timings", "bem_operator_reassemble", "bem_operator_export_pattern", "bem_operator_pattern_rows",
     "bem_operator_export_dense", "bem_operator_entries", "bem_operator_destroy",
     "bem_rhs", "bem_matvec", "bem_solve", "bem_solve_device", "bem_inner_potentials",
 ]
@@ -90,8 +90,10 @@ def load(build_if_missing: bool = False):
     L.bem_operator_stats.argtypes = [VP, I64, I64, I64, D]
     L.bem_operator_reassemble.argtypes = [VP, VP]
     L.bem_operator_timings.argtypes = [VP, D]
+    L.bem_operator_check.argtypes = [VP, I64, D]
     L.bem_operator_export_pattern.argtypes = [VP, I64, I32]
     L.bem_operator_export_dense.argtypes = [VP, D]
+    L.bem_operator_pattern_rows.argtypes = [VP, ctypes.c_int64, I32, ctypes.c_int64, I64, I32]
     L.bem_operator_entries.argtypes = [VP, ctypes.c_int64, I32, D]
     L.bem_operator_destroy.argtypes = [VP]
     L.bem_operator_destroy.restype = None

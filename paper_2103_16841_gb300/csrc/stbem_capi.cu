@@ -384,8 +384,9 @@ bem_status assemble(bem_operator* op, cudaStream_t s, bool first) {
   }
   if (first) {
     op->nstored = vo; op->nrows_stored = ro; op->nnz = nnz; op->nblocks = nblk;
-    TRY(dalloc(&op->d_val, (size_t)vo));
-    if (op->opts.store_fp32) TRY(dalloc(&op->d_val32, (size_t)vo));
+    // mixed-precision values carry FP32 accuracy: FP32 storage only
+    if (op->opts.precision == BEM_PREC_FP64) TRY(dalloc(&op->d_val, (size_t)vo));
+    if (op->opts.store_fp32 || op->opts.precision == BEM_PREC_MIXED) TRY(dalloc(&op->d_val32, (size_t)vo));
     TRY(dalloc(&op->d_rs, (size_t)ro));
     int grid = quad_grid(op);
     op->tmp_len = std::max<int64_t>((int64_t)grid * m->max_col_surf * m->max_col_tets, 2 * m->n_tet * 8);
@@ -445,7 +446,25 @@ bem_status bem_operator_create(bem_context* ctx, const bem_mesh* mesh, const bem
   TRY(dalloc(&op->d_counter, 4));
   bem_status st = assemble(op.get(), ctx->stream, true);
   if (st != BEM_OK) { bem_operator_destroy(op.release()); return st; }
+  int64_t nbad = 0;
+  double mx = 0.0;
+  st = op_value_scan(op.get(), &nbad, &mx, ctx->stream);
+  if (st == BEM_OK && nbad > 0) {
+    set_error(std::to_string(nbad) + " assembled values are not finite");
+    st = BEM_ERR_INTERNAL;
+  }
+  if (st != BEM_OK) { bem_operator_destroy(op.release()); return st; }
   *out = op.release();
+  return BEM_OK;
+}
+
+bem_status bem_operator_check(const bem_operator* op, int64_t* n_nonfinite, double* max_abs) {
+  if (!op) { set_error("null operator"); return BEM_ERR_INVALID_ARG; }
+  int64_t nb = 0;
+  double mx = 0.0;
+  TRY(op_value_scan(op, &nb, &mx, op->ctx->stream));
+  if (n_nonfinite) *n_nonfinite = nb;
+  if (max_abs) *max_abs = mx;
   return BEM_OK;
 }
 
@@ -511,6 +530,52 @@ bem_status bem_operator_export_pattern(const bem_operator* op, int64_t* rowptr, 
   return BEM_OK;
 }
 
+bem_status bem_operator_pattern_rows(const bem_operator* op, int64_t n, const int32_t* rows, int64_t cap,
+                                     int64_t* counts, int32_t* cols) {
+  if (!op || n < 0 || (n > 0 && (!rows || !counts || (cap > 0 && !cols))) || cap < 0) {
+    set_error("bem_operator_pattern_rows: invalid argument");
+    return BEM_ERR_INVALID_ARG;
+  }
+  const bem_mesh* m = op->mesh;
+  cudaStream_t s = op->ctx->stream;
+  std::vector<int32_t> internal(n);
+  std::vector<int64_t> colset;
+  for (int64_t k = 0; k < n; ++k) {
+    if (rows[k] < 0 || rows[k] >= m->n_tet) { set_error("row out of range"); return BEM_ERR_INVALID_ARG; }
+    internal[k] = m->iperm[rows[k]];
+    auto it = std::upper_bound(m->col_tet_begin.begin(), m->col_tet_begin.end(), internal[k]);
+    colset.push_back((int64_t)(it - m->col_tet_begin.begin()) - 1);
+  }
+  std::sort(colset.begin(), colset.end());
+  colset.erase(std::unique(colset.begin(), colset.end()), colset.end());
+  const int64_t nt = m->n_tet;
+  DevBuf<int64_t> cnt, rp;
+  TRY(cnt.alloc(nt)); TRY(rp.alloc(nt + 1));
+  STBEM_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int64_t) * nt, s));
+  for (int64_t I : colset) TRY(op_pattern_csr(op, cnt.p, rp.p, nullptr, false, s, I));
+  std::vector<int64_t> hc(nt), hp(nt + 1, 0);
+  STBEM_CUDA(cudaMemcpyAsync(hc.data(), cnt.p, sizeof(int64_t) * nt, cudaMemcpyDeviceToHost, s));
+  STBEM_CUDA(cudaStreamSynchronize(s));
+  for (int64_t i = 0; i < nt; ++i) hp[i + 1] = hp[i] + hc[i];
+  DevBuf<int32_t> cl;
+  TRY(cl.alloc(std::max<int64_t>(hp[nt], 1)));
+  STBEM_CUDA(cudaMemcpyAsync(rp.p, hp.data(), sizeof(int64_t) * (nt + 1), cudaMemcpyHostToDevice, s));
+  STBEM_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int64_t) * nt, s));
+  for (int64_t I : colset) TRY(op_pattern_csr(op, cnt.p, rp.p, cl.p, true, s, I));
+  std::vector<int32_t> hcl(std::max<int64_t>(hp[nt], 1));
+  STBEM_CUDA(cudaMemcpyAsync(hcl.data(), cl.p, sizeof(int32_t) * hp[nt], cudaMemcpyDeviceToHost, s));
+  STBEM_CUDA(cudaStreamSynchronize(s));
+  for (int64_t k = 0; k < n; ++k) {
+    int32_t i = internal[k];
+    std::vector<int32_t> row(hcl.begin() + hp[i], hcl.begin() + hp[i + 1]);
+    for (auto& j : row) j = m->perm[j];
+    std::sort(row.begin(), row.end());
+    counts[k] = (int64_t)row.size();
+    for (int64_t q = 0; q < std::min<int64_t>(cap, (int64_t)row.size()); ++q) cols[k * cap + q] = row[q];
+  }
+  return BEM_OK;
+}
+
 bem_status bem_operator_export_dense(const bem_operator* op, double* A) {
   if (!op || !A) { set_error("invalid argument"); return BEM_ERR_INVALID_ARG; }
   const bem_mesh* m = op->mesh;
@@ -520,12 +585,18 @@ bem_status bem_operator_export_dense(const bem_operator* op, double* A) {
   std::vector<int32_t> bw(nb), rs(std::max<int64_t>(op->nrows_stored, 1));
   std::vector<int64_t> boff(nb), rsoff(nb);
   std::vector<double> val(std::max<int64_t>(op->nstored, 1));
+  std::vector<float> val32(op->d_val ? 1 : std::max<int64_t>(op->nstored, 1));
   STBEM_CUDA(cudaMemcpyAsync(bw.data(), op->d_bw, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, s));
   STBEM_CUDA(cudaMemcpyAsync(boff.data(), op->d_boff, sizeof(int64_t) * nb, cudaMemcpyDeviceToHost, s));
   STBEM_CUDA(cudaMemcpyAsync(rsoff.data(), op->d_rsoff, sizeof(int64_t) * nb, cudaMemcpyDeviceToHost, s));
   STBEM_CUDA(cudaMemcpyAsync(rs.data(), op->d_rs, sizeof(int32_t) * op->nrows_stored, cudaMemcpyDeviceToHost, s));
-  STBEM_CUDA(cudaMemcpyAsync(val.data(), op->d_val, sizeof(double) * op->nstored, cudaMemcpyDeviceToHost, s));
+  if (op->d_val)
+    STBEM_CUDA(cudaMemcpyAsync(val.data(), op->d_val, sizeof(double) * op->nstored, cudaMemcpyDeviceToHost, s));
+  else
+    STBEM_CUDA(cudaMemcpyAsync(val32.data(), op->d_val32, sizeof(float) * op->nstored, cudaMemcpyDeviceToHost, s));
   STBEM_CUDA(cudaStreamSynchronize(s));
+  if (!op->d_val)
+    for (int64_t k = 0; k < op->nstored; ++k) val[k] = (double)val32[k];
   std::memset(A, 0, sizeof(double) * n * n);
   for (int64_t I = 0; I < m->n_col; ++I) {
     int t0 = m->col_tet_begin[I], R = m->col_tet_begin[I + 1] - t0;
@@ -611,7 +682,7 @@ bem_status bem_solve_device(bem_operator* op, const double* b_dev, double* w_dev
     set_error("bem_solve: bad options");
     return BEM_ERR_INVALID_ARG;
   }
-  if (o.inner_dtype == BEM_DTYPE_FP32 && !op->d_val32) {
+  if (o.inner_dtype == BEM_DTYPE_FP32 && !op->d_val32 && op->d_val) {
     set_error("FP32 inner solves need store_fp32 = 1");
     return BEM_ERR_INVALID_ARG;
   }

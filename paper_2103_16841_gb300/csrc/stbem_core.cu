@@ -13,11 +13,18 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "stbem_internal.h"
 
 namespace stbem {
+
+static double __longlong_as_double_host(long long b) {
+  double d;
+  std::memcpy(&d, &b, sizeof(d));
+  return d;
+}
 
 bem_status upload_gauss_tables() {
   std::vector<double> X(MAX_NTHETA * (MAX_NTHETA + 1) / 2), W(X.size());
@@ -180,10 +187,12 @@ struct TetSm {       // panel data kept in shared memory for a block
   double tmin, pmax;
   double vt[4];
   double ball[5];
+  float vtf[4];      // FP32 copies for the filter of the sparsity predicate
+  float ballf[5];
   int32_t lo, hi, dup, pad;
 };
 
-__device__ bool c2_exact(const double* x, const TetSm& T, const ColGeom& G) {
+__device__ __noinline__ bool c2_exact(const double* x, const TetSm& T, const ColGeom& G) {
   double mx = -INFINITY;
   for (int b = 0; b < 4; ++b) {
     int k = b < 3 ? b : T.dup;
@@ -192,7 +201,7 @@ __device__ bool c2_exact(const double* x, const TetSm& T, const ColGeom& G) {
   }
   return mx >= 0.0;
 }
-__device__ bool c3_fail_exact(const double* x, const TetSm& T) {
+__device__ __noinline__ bool c3_fail_exact(const double* x, const TetSm& T) {
   double al = dist3x(x + 1, T.ball + 1);
   double phi = __dsub_rn(al, __dsub_rn(x[0], T.ball[0]));
   double rj = T.ball[4];
@@ -210,7 +219,7 @@ __device__ bool point_sees(const double* x, const float* xf, const TetSm& T, con
     bool sure_true = false, sure_false = true;
     for (int b = 0; b < 4; ++b) {
       int k = b < 3 ? b : T.dup;
-      float v = dist3f(xf + 1, Xf[k]) - (xf[0] - (float)T.vt[b]);
+      float v = dist3f(xf + 1, Xf[k]) - (xf[0] - T.vtf[b]);
       if (v > margin) sure_true = true;
       if (!(v < -margin)) sure_false = false;
     }
@@ -221,10 +230,9 @@ __device__ bool point_sees(const double* x, const float* xf, const TetSm& T, con
   }
   // C3
   {
-    float bc[3] = {(float)T.ball[1], (float)T.ball[2], (float)T.ball[3]};
-    float al = dist3f(xf + 1, bc);
-    float phi = al - (xf[0] - (float)T.ball[0]);
-    float rj = (float)T.ball[4];
+    float al = dist3f(xf + 1, T.ballf + 1);
+    float phi = al - (xf[0] - T.ballf[0]);
+    float rj = T.ballf[4];
     float dr = (al < rj * 0.70710678f) ? al + sqrtf(fmaxf(rj * rj - al * al, 0.f)) : rj * 1.41421356f;
     float v = phi - dr;
     if (v > margin) return false;
@@ -309,8 +317,8 @@ __device__ void load_column(const BlockCtx& B, int64_t J, ColSm& C, TetSm* T, Fa
     const TetDev& D = B.tets[C.tet0 + j];
     TetSm t;
     t.tmin = D.tmin; t.pmax = D.pmax;
-    for (int k = 0; k < 4; ++k) t.vt[k] = D.vt[k];
-    for (int k = 0; k < 5; ++k) t.ball[k] = D.ball[k];
+    for (int k = 0; k < 4; ++k) { t.vt[k] = D.vt[k]; t.vtf[k] = (float)D.vt[k]; }
+    for (int k = 0; k < 5; ++k) { t.ball[k] = D.ball[k]; t.ballf[k] = (float)D.ball[k]; }
     t.lo = D.lo - C.surf0; t.hi = D.hi - C.surf0; t.dup = D.dup; t.pad = 0;
     T[j] = t;
   }
@@ -425,7 +433,7 @@ __global__ void __launch_bounds__(128) k_pattern_blocks(BlockCtx B) {
 
 // Pass 2: quadrature and assembly of every non-empty block.
 template <bool FP32>
-__global__ void __launch_bounds__(128) k_quad_blocks(BlockCtx B) {
+__global__ void __launch_bounds__(128, 4) k_quad_blocks(BlockCtx B) {
   typedef typename std::conditional<FP32, float, double>::type R;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ColSm C;
@@ -502,7 +510,7 @@ __global__ void __launch_bounds__(128) k_quad_blocks(BlockCtx B) {
             cls = face_class(C.G, mypc[q], Fs[slo + s], Fv, cc);
           }
           if (cls == FACE_CUT) cut = true;
-          else Wsc[q * B.max_surf + s] = cls == FACE_LIT ? (R)mypc[q].Wst : R(0);
+          else Wsc[q * B.max_surf + s] = cls == FACE_LIT ? (FP32 ? (R)mypc[q].Wst_f : (R)mypc[q].Wst) : R(0);
         }
         unsigned mk = __ballot_sync(0xffffffffu, cut);
         if (cut) mycut[ncut + __popc(mk & ((1u << lane) - 1u))] = (uint16_t)it;
@@ -557,7 +565,7 @@ __global__ void __launch_bounds__(128) k_quad_blocks(BlockCtx B) {
         int j = first + w;
         R v = R(0);
         if (j < ntJ) v = scale * (Ulo[j] - Uhi[j]);
-        B.val[voff + (int64_t)w * nt + r] = (double)v;
+        if (B.val) B.val[voff + (int64_t)w * nt + r] = (double)v;
         if (B.val32) B.val32[voff + (int64_t)w * nt + r] = (float)v;
       }
     }
@@ -696,6 +704,7 @@ __global__ void k_matvec(int64_t n_col, const int32_t* col_tet_begin, const int3
 
 bem_status op_matvec(const bem_operator* op, const double* x, double* y, int nrhs, bool fp32, cudaStream_t s) {
   const bem_mesh* m = op->mesh;
+  if (!op->d_val) fp32 = true;  // mixed-precision operators keep FP32 values only
   int rows_pad = ((m->max_col_tets + 31) / 32) * 32;
   int groups = std::max(1, std::min(8, 512 / rows_pad));
   int threads = rows_pad * groups;
@@ -715,9 +724,53 @@ bem_status op_matvec(const bem_operator* op, const double* x, double* y, int nrh
 }
 
 // ---------------------------------------------------------------------------
+// Value scan: non-finite count and largest magnitude
+// ---------------------------------------------------------------------------
+template <typename V>
+__global__ void k_value_scan(const V* v, int64_t n, unsigned long long* bad, unsigned long long* maxbits) {
+  unsigned long long nb = 0;
+  double mx = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double x = (double)v[i];
+    if (!isfinite(x)) ++nb;
+    else mx = fmax(mx, fabs(x));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    nb += __shfl_xor_sync(0xffffffffu, nb, o);
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (nb) atomicAdd(bad, nb);
+    atomicMax(maxbits, (unsigned long long)__double_as_longlong(mx));  // non-negative doubles order as integers
+  }
+}
+
+bem_status op_value_scan(const bem_operator* op, int64_t* nbad, double* maxabs, cudaStream_t s) {
+  unsigned long long* d;
+  STBEM_CUDA(cudaMalloc(&d, 2 * sizeof(unsigned long long)));
+  STBEM_CUDA(cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), s));
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (op->nstored > 0) {
+    if (op->d_val) k_value_scan<double><<<sms * 8, 256, 0, s>>>(op->d_val, op->nstored, d, d + 1);
+    else k_value_scan<float><<<sms * 8, 256, 0, s>>>(op->d_val32, op->nstored, d, d + 1);
+  }
+  unsigned long long h[2];
+  cudaError_t e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return BEM_ERR_CUDA; }
+  *nbad = (int64_t)h[0];
+  long long bits = (long long)h[1];
+  *maxabs = __longlong_as_double_host(bits);
+  return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Entry lookup (internal indices) and pattern CSR export
 // ---------------------------------------------------------------------------
-__global__ void k_entries(int64_t n, const int32_t* ij, const int32_t* iperm_unused, const TetDev* tets, int64_t n_col,
+__global__ void k_entries(int64_t n, const int32_t* ij, const float* val32, const TetDev* tets, int64_t n_col,
                           const int32_t* col_tet_begin, const int32_t* bw, const int64_t* boff, const int64_t* rsoff,
                           const int32_t* rs, const double* val, double* out) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -732,7 +785,7 @@ __global__ void k_entries(int64_t n, const int32_t* ij, const int32_t* iperm_unu
     int nt = col_tet_begin[I + 1] - col_tet_begin[I];
     int start = rs[rsoff[b] + r];
     int w = j - start;
-    if (w >= 0 && w < W) v = val[boff[b] + (int64_t)w * nt + r];
+    if (w >= 0 && w < W) v = val ? val[boff[b] + (int64_t)w * nt + r] : (double)val32[boff[b] + (int64_t)w * nt + r];
   }
   out[k] = v;
 }
@@ -740,7 +793,7 @@ __global__ void k_entries(int64_t n, const int32_t* ij, const int32_t* iperm_unu
 bem_status op_entries(const bem_operator* op, int64_t n, const int32_t* d_ij, double* d_out, cudaStream_t s) {
   const bem_mesh* m = op->mesh;
   if (n == 0) return BEM_OK;
-  k_entries<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, d_ij, nullptr, m->d_tet, m->n_col, m->d_col_tet_begin,
+  k_entries<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, d_ij, op->d_val32, m->d_tet, m->n_col, m->d_col_tet_begin,
                                                        op->d_bw, op->d_boff, op->d_rsoff, op->d_rs, op->d_val, d_out);
   STBEM_CUDA(cudaGetLastError());
   return BEM_OK;
@@ -749,17 +802,18 @@ bem_status op_entries(const bem_operator* op, int64_t n, const int32_t* d_ij, do
 // Pattern rows (internal numbering): count pass, then fill pass (columns are
 // written in internal order; the caller permutes and sorts).
 __global__ void __launch_bounds__(128) k_pattern_rows(BlockCtx B, int64_t* rowcount, const int64_t* rowptr,
-                                                      int32_t* cols, int fill) {
+                                                      int32_t* cols, int fill, int64_t I_only) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ColSm C;
   TetSm* T = reinterpret_cast<TetSm*>(smem);
   FaceGeom* Fs = reinterpret_cast<FaceGeom*>(T + B.max_tet);
   uint32_t* bits = reinterpret_cast<uint32_t*>(Fs + B.max_surf);
   const int words = (B.max_tet + 31) / 32;
-  const int64_t nblk = B.n_col * B.n_col;
+  const int64_t nblk = I_only >= 0 ? B.n_col : B.n_col * B.n_col;
   for (;;) {
     int64_t b = pop_block(B);
     if (b >= nblk) break;
+    if (I_only >= 0) b += I_only * B.n_col;
     if (B.bw[b] == 0) continue;
     int64_t I = b / B.n_col, J = b % B.n_col;
     load_column(B, J, C, T, Fs);
@@ -797,14 +851,14 @@ __global__ void __launch_bounds__(128) k_pattern_rows(BlockCtx B, int64_t* rowco
 }
 
 bem_status op_pattern_csr(const bem_operator* op, int64_t* d_rowcount, int64_t* d_rowptr, int32_t* d_cols, bool fill,
-                          cudaStream_t s) {
+                          cudaStream_t s, int64_t I_only) {
   BlockCtx B = make_ctx(const_cast<bem_operator*>(op));
   bem_status st = get_counter(op, &B.counter, s);
   if (st != BEM_OK) return st;
   size_t smem = block_smem(op, false);
   STBEM_CUDA(cudaFuncSetAttribute(k_pattern_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int grid = persistent_grid((const void*)k_pattern_rows, smem, 128);
-  k_pattern_rows<<<grid, 128, smem, s>>>(B, d_rowcount, d_rowptr, d_cols, fill ? 1 : 0);
+  k_pattern_rows<<<grid, 128, smem, s>>>(B, d_rowcount, d_rowptr, d_cols, fill ? 1 : 0, I_only);
   STBEM_CUDA(cudaGetLastError());
   return BEM_OK;
 }

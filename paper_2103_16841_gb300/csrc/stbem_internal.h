@@ -101,9 +101,10 @@ bem_status op_pattern(bem_operator* op, cudaStream_t s);
 bem_status op_quadrature(bem_operator* op, cudaStream_t s);
 bem_status op_matvec(const bem_operator* op, const double* x, double* y, int nrhs, bool fp32, cudaStream_t s);
 bem_status op_rhs(const bem_operator* op, int kind, int nrhs, const double* d_params, double* d_b, cudaStream_t s);
+bem_status op_value_scan(const bem_operator* op, int64_t* nbad, double* maxabs, cudaStream_t s);
 bem_status op_entries(const bem_operator* op, int64_t n, const int32_t* d_ij, double* d_out, cudaStream_t s);
 bem_status op_pattern_csr(const bem_operator* op, int64_t* d_rowcount, int64_t* d_rowptr, int32_t* d_cols,
-                          bool fill, cudaStream_t s);
+                          bool fill, cudaStream_t s, int64_t I_only = -1);
 bem_status inner_potentials(int64_t n, const double* d_x4, const double* d_tets, const int32_t* d_sv, int prec,
                             int n_theta, double* d_out, cudaStream_t s);
 bem_status permute(const int32_t* d_perm, const double* in, double* out, int64_t n, int nrhs, bool to_internal,

@@ -98,6 +98,7 @@ struct PointCol {        // apex x against one column
   double r[3];           // |x_s - corner_k| (FP64: the cone-function values need it)
   double rlo;            // lower bound of dist(x_s, K)
   double Wst;            // 4 pi * potential of the whole triangle
+  float Wst_f;
   int inK;
   PtR<double> D;
   PtR<float> F;          // filled for the mixed-precision path
@@ -198,50 +199,77 @@ STBEM_HD inline void fill_pt(PtR<R>& T, const PtR<double>& D, const ColGeom& G, 
   }
 }
 
-// Geometry of apex x against column G (FP64) and the whole-triangle
-// potential (the fully lit case), in FP64 or (prec_fp32) with FP32 closed forms.
+// Geometry of apex x against column G and the whole-triangle potential (the
+// fully lit case). FP64 path: everything in FP64. Mixed path: the relative
+// position, the height d, the foot point and the corner distances in FP64
+// (they carry the cancellation between |x - y| and t - tau), the rest in FP32.
 STBEM_HD inline void point_col(const double* x, const ColGeom& G, PointCol& P, bool prec_fp32) {
   P.t = x[0];
   double rel[3] = {x[1] - G.c0[0], x[2] - G.c0[1], x[3] - G.c0[2]};
   double d = rel[0] * G.n[0] + rel[1] * G.n[1] + rel[2] * G.n[2];
   if (fabs(d) < 1e-13 * G.diam) d = 0.0;
+  double xb0 = rel[0] * G.e1[0] + rel[1] * G.e1[1] + rel[2] * G.e1[2];
+  double xb1 = rel[0] * G.e2[0] + rel[1] * G.e2[1] + rel[2] * G.e2[2];
+  for (int k = 0; k < 3; ++k) {
+    double dx = x[1] - G.X[k][0], dy = x[2] - G.X[k][1], dz = x[3] - G.X[k][2];
+    P.r[k] = sqrt(dx * dx + dy * dy + dz * dz);
+  }
+  if (prec_fp32) {
+    PtR<float>& T = P.F;
+    T.d = (float)d;
+    T.xb[0] = (float)xb0;
+    T.xb[1] = (float)xb1;
+    int in = 1;
+    float out = 0.f, W = 0.f;
+    for (int k = 0; k < 3; ++k) {
+      T.q[k][0] = (float)G.Q[k][0] - T.xb[0];
+      T.q[k][1] = (float)G.Q[k][1] - T.xb[1];
+      T.rs[k] = (float)P.r[k];
+    }
+    for (int k = 0; k < 3; ++k) {
+      float ux = (float)G.U[k][0], uy = (float)G.U[k][1];
+      T.ps[k] = T.q[k][0] * uy - T.q[k][1] * ux;
+      T.ws[k] = T.q[k][0] * ux + T.q[k][1] * uy;
+      if (!(T.ps[k] > 0.f)) in = 0;
+      out = fmaxf(out, -T.ps[k]);
+      T.Efull[k] = edge_dE<float>(T.ws[k], T.ws[k] + (float)G.L[k], T.ps[k], T.d);
+      W += T.Efull[k];
+      split2(P.r[k] - P.t, P.rho_hi[k], P.rho_lo[k]);
+    }
+    P.inK = in;
+    P.rlo = sqrt(d * d + (double)out * (double)out);
+    P.Wst = (double)W;
+    P.Wst_f = W;
+    P.D.d = d;
+    P.D.xb[0] = xb0;
+    P.D.xb[1] = xb1;
+    split2(-P.t, P.nt_hi, P.nt_lo);
+    split2(P.rlo - P.t, P.rlot_hi, P.rlot_lo);
+    return;
+  }
   PtR<double>& D = P.D;
   D.d = d;
-  D.xb[0] = rel[0] * G.e1[0] + rel[1] * G.e1[1] + rel[2] * G.e1[2];
-  D.xb[1] = rel[0] * G.e2[0] + rel[1] * G.e2[1] + rel[2] * G.e2[2];
+  D.xb[0] = xb0;
+  D.xb[1] = xb1;
   int in = 1;
-  double out = 0.0;
+  double out = 0.0, W = 0.0;
   for (int k = 0; k < 3; ++k) {
     D.q[k][0] = G.Q[k][0] - D.xb[0];
     D.q[k][1] = G.Q[k][1] - D.xb[1];
-    double dx = x[1] - G.X[k][0], dy = x[2] - G.X[k][1], dz = x[3] - G.X[k][2];
-    P.r[k] = sqrt(dx * dx + dy * dy + dz * dz);
+    D.rs[k] = P.r[k];
   }
   for (int k = 0; k < 3; ++k) {
     D.ps[k] = D.q[k][0] * G.U[k][1] - D.q[k][1] * G.U[k][0];
     D.ws[k] = D.q[k][0] * G.U[k][0] + D.q[k][1] * G.U[k][1];
-    D.rs[k] = P.r[k];
     if (!(D.ps[k] > 0.0)) in = 0;
     out = fmax(out, -D.ps[k]);
+    D.Efull[k] = edge_dE<double>(D.ws[k], D.ws[k] + G.L[k], D.ps[k], d);
+    W += D.Efull[k];
   }
   P.inK = in;
   P.rlo = sqrt(d * d + out * out);
-  double W = 0.0;
-  if (prec_fp32) {
-    fill_pt<float>(P.F, D, G, P.r);
-    for (int k = 0; k < 3; ++k) {
-      W += (double)P.F.Efull[k];
-      split2(P.r[k] - P.t, P.rho_hi[k], P.rho_lo[k]);
-    }
-    split2(-P.t, P.nt_hi, P.nt_lo);
-    split2(P.rlo - P.t, P.rlot_hi, P.rlot_lo);
-  } else {
-    for (int k = 0; k < 3; ++k) {
-      D.Efull[k] = edge_dE<double>(D.ws[k], D.ws[k] + G.L[k], D.ps[k], d);
-      W += D.Efull[k];
-    }
-  }
   P.Wst = W;
+  P.Wst_f = (float)W;
 }
 
 // ---------------------------------------------------------------------------
@@ -376,6 +404,7 @@ STBEM_HD inline ArcRule make_rule(int precision_mixed, int n_max) {
 template <typename R>
 STBEM_HD __noinline__ R arc_piece(const ArcFrame<R>& F, R lo, R hi, const ArcRule& rule) {
   R mid = R(0.5) * (lo + hi), half = R(0.5) * (hi - lo);
+  if (!(half > R(0))) return R(0);
   R best_rho = R(1e30), best_a = R(0), best_b = R(1e30);
   {
     // poles of I: L1 = 1 - <g, n_par> = 0 (r -> infinity) and
@@ -405,6 +434,9 @@ STBEM_HD __noinline__ R arc_piece(const ArcFrame<R>& F, R lo, R hi, const ArcRul
     R a = best_a, b = best_b;
     if (a > R(1)) { b = sqrt((a - R(1)) * (a - R(1)) + b * b); a = R(1); }
     else if (a < R(-1)) { b = sqrt((a + R(1)) * (a + R(1)) + b * b); a = R(-1); }
+    // a pole computed on the interval itself (rounding of a real pole that
+    // lies just outside): keep the map finite
+    b = fmax(b, R(sizeof(R) == 4 ? 1e-5 : 1e-12));
     R s1 = asinh((R(1) + a) / b), s2 = asinh((R(1) - a) / b);
     R mu = R(0.5) * (s1 + s2), et = R(0.5) * (s1 - s2);
     for (int k = 0; k < n; ++k) {
@@ -445,7 +477,7 @@ STBEM_HD inline R arc_d0_U(R psi, R e) {
 }
 
 template <typename R>
-STBEM_HD inline R arc_d0(const R* A, const R* B, bool full, R c, const R* g) {
+STBEM_HD __noinline__ R arc_d0(const R* A, const R* B, bool full, R c, const R* g) {
   if (c == R(0)) return R(0);
   const R pi = (R)STBEM_PI, twopi = (R)(2.0 * STBEM_PI);
   R G0 = sqrt(g[0] * g[0] + g[1] * g[1]);
@@ -677,10 +709,13 @@ STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, con
       for (int i = 0; i < nr; ++i)
         if (a0 - a1 * rt[i] > R(0) && rt[i] >= -slack && rt[i] <= R(1) + slack) v[nv++] = fmin(R(1), fmax(R(0), rt[i]));
       if (nv == 2 && v[0] > v[1]) { R tmp = v[0]; v[0] = v[1]; v[1] = tmp; }
+      // F is convex along the edge: with F(0) < 0 <= F(1) its root in [0, 1] is
+      // the larger one (the other lies before the edge start); with
+      // F(0) >= 0 > F(1) it is the smaller one
       if (F[k] < R(0)) {           // exit on this edge
-        lb = nv ? v[0] : R(1); lb_root = nv > 0; has = true;
+        lb = nv ? v[nv - 1] : R(1); lb_root = nv > 0; has = true;
       } else if (F[k1] < R(0)) {   // entry on this edge
-        la = nv ? v[nv - 1] : R(0); la_root = nv > 0; has = true;
+        la = nv ? v[0] : R(0); la_root = nv > 0; has = true;
       } else if (nv == 2 && v[1] > v[0]) {
         la = v[0]; lb = v[1]; la_root = lb_root = true; has = true;
       }

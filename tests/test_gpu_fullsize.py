@@ -1,0 +1,136 @@
+"""GPU checks at full workload size, in the launch configuration bench.py times
+(icosphere level 3, T = 4, 32 jittered slabs, mixed precision, m_Q = 3).
+
+The oracle cannot assemble 1e9 pairs, so it checks sampled pattern rows
+(bit-exact) and sampled entries computed one by one; properties that hold at
+any size (finite values, solver convergence, agreement of the precisions,
+convergence in h on the sphere) cover the rest.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_16841_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+NT = os.cpu_count()
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2103_16841_gb300 as stb
+    return stb.Context(0)
+
+
+def _row_check(op, m, nrows, tol, seed):
+    om = oracle.Mesh.from_spacetime(m)
+    rng = np.random.default_rng(seed)
+    rows = rng.choice(m.n_tet, nrows, replace=False).astype(np.int32)
+    g_rows = op.pattern_rows(rows)
+    o_rows = om.pattern_rows(rows)
+    for r, a, b in zip(rows, g_rows, o_rows):
+        assert np.array_equal(a, b), f"pattern row {r} differs"
+    pairs = np.array([(r, c) for r, cs in zip(rows, o_rows) for c in cs], dtype=np.int32)
+    pick = pairs[rng.choice(len(pairs), min(600, len(pairs)), replace=False)]
+    g = op.entries(pick)
+    o = om.entries(pick, nthreads=NT)
+    scale = np.abs(o).max()
+    err = np.abs(g - o).max() / scale
+    assert err <= tol, err
+    return err
+
+
+@pytest.fixture(scope="module")
+def c2_mixed(ctx):
+    import paper_2103_16841_gb300 as stb
+    m = inputs.workload_c2()
+    mesh = stb.Mesh.from_spacetime(ctx, m)
+    op = stb.Operator(ctx, mesh, "mixed")
+    return m, mesh, op
+
+
+def test_c2_mixed_values_finite(c2_mixed):
+    m, mesh, op = c2_mixed
+    nbad, mx = op.check()
+    assert nbad == 0 and 0 < mx < 1.0
+
+
+def test_c2_mixed_pattern_rows_and_entries(c2_mixed):
+    m, mesh, op = c2_mixed
+    _row_check(op, m, 6, 1e-6, seed=21)
+
+
+def test_c2_mixed_solve_converges(c2_mixed):
+    m, mesh, op = c2_mixed
+    import paper_2103_16841_gb300 as stb
+    b = op.rhs(stb.DATA_PULSE, inputs.pulse_params(1, seed=2, fixed_c=1.5))[:, 0]
+    w, info = op.solve(b, tol=1e-8, restart=50, maxit=400, inner="fp32", max_refine=8)
+    assert info[0]["converged"] and info[0]["rel_residual"] <= 1e-8
+    assert np.isfinite(w).all()
+
+
+def test_l3x16_fp64_pattern_rows_and_entries(ctx):
+    import paper_2103_16841_gb300 as stb
+    m = inputs.sphere_mesh(3, 16, 4.0, 0.2, seed=4)
+    mesh = stb.Mesh.from_spacetime(ctx, m)
+    op = stb.Operator(ctx, mesh, "fp64", store_fp32=False)
+    assert op.check()[0] == 0
+    _row_check(op, m, 4, 1e-11, seed=22)
+
+
+def test_mixed_solution_matches_fp64(ctx):
+    """Reduced-precision form: the mixed-precision operator's solution against
+    the FP64 one, pulse data on the level-2 sphere with 8 jittered slabs."""
+    import paper_2103_16841_gb300 as stb
+    m = inputs.sphere_mesh(2, 8, 2.0, 0.2, seed=3)
+    mesh = stb.Mesh.from_spacetime(ctx, m)
+    op64 = stb.Operator(ctx, mesh, "fp64")
+    opm = stb.Operator(ctx, mesh, "mixed")
+    prm = inputs.pulse_params(4, seed=2)
+    b = op64.rhs(stb.DATA_PULSE, prm)
+    w64, _ = op64.solve(b, tol=1e-12, restart=100, maxit=3000)
+    wm, info = opm.solve(b, tol=1e-12, restart=100, maxit=1000, inner="fp32", max_refine=12)
+    rel = np.linalg.norm(wm - w64, axis=0) / np.linalg.norm(w64, axis=0)
+    assert all(i["converged"] for i in info)
+    assert rel.max() <= 1e-5, rel
+
+
+def _l2_error(m, w):
+    """||phi - w_h|| / ||phi|| in L2(Sigma); phi depends on time only, the panel
+    integrals use the degree-2 four-point tetrahedral rule."""
+    X = m.stv_xyzt()
+    T = X[m.tets]                                    # [n, 4, 4]
+    E = T[:, 1:, :] - T[:, :1, :]
+    vol = np.sqrt(np.maximum(np.linalg.det(E @ np.transpose(E, (0, 2, 1))), 0.0)) / 6.0
+    a, bq = 0.5854101966249685, 0.1381966011250105
+    L = np.full((4, 4), bq) + np.eye(4) * (a - bq)   # barycentric weights of the 4 nodes
+    tq = T[:, :, 0] @ L.T                            # [n, 4] node times
+    ex = np.pi * np.sin(np.pi * tq)
+    err2 = np.sum(vol[:, None] / 4 * (ex - w[:, None]) ** 2)
+    ref2 = np.sum(vol[:, None] / 4 * ex ** 2)
+    return math.sqrt(err2 / ref2)
+
+
+def test_sphere_convergence_in_h(ctx):
+    """Sphere closed form: V phi = 1/2 int_0^min(t,2) phi(t-r) dr, so g = sin^2(pi t/2)
+    on [0, 2] has phi = pi sin(pi t); the Galerkin L2(Sigma) error falls with h
+    at fixed dt/h (first order expected)."""
+    import paper_2103_16841_gb300 as stb
+    errs = []
+    for level, slabs in [(1, 4), (2, 8), (3, 16)]:
+        m = inputs.sphere_mesh(level, slabs, 2.0, 0.0)
+        mesh = stb.Mesh.from_spacetime(ctx, m)
+        op = stb.Operator(ctx, mesh, "mixed")
+        b = op.rhs(stb.DATA_SIN2_UNIFORM)[:, 0]
+        w, info = op.solve(b, tol=1e-10, restart=100, maxit=3000, inner="fp32", max_refine=10)
+        assert info[0]["converged"]
+        errs.append(_l2_error(m, w))
+    print("e_BEM by level:", errs)
+    assert errs[1] < errs[0] and errs[2] < errs[1]
+    assert errs[2] < 0.6 * errs[0]
