@@ -199,6 +199,22 @@ bem_status bem_rhs(const bem_operator* op, int32_t kind, int32_t nrhs, const dou
  * enqueued on `stream` (a cudaStream_t; NULL = context stream). */
 bem_status bem_matvec(const bem_operator* op, const double* x_dev, double* y_dev, int32_t nrhs, void* stream);
 
+/* Allocation-free y_dev = A x_dev (no counterpart in the paper: it exists for
+ * callers that cannot let a library allocate device memory while they run,
+ * such as a serving loop or runtime that reserves all device memory up front,
+ * or code on a latency budget where cudaMalloc/cudaFree cost time and
+ * cudaFree synchronizes the device). Same arguments and result as bem_matvec,
+ * but the two temporary vectors of the caller/internal reordering come from a
+ * fixed array compiled into the library (2 x 2^20 doubles, 16 MiB, held on
+ * every GPU that loads the library until exit), so n_tet * nrhs must not
+ * exceed 1,048,576 (BEM_ERR_INVALID_ARG otherwise). It calls no allocator.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture. The call is
+ * enqueued on `stream` and returns without synchronizing. All calls share the
+ * array: calls whose work overlaps on the GPU (other streams, other threads)
+ * race on it and must be ordered by the caller. */
+bem_status bem_matvec_noalloc(const bem_operator* op, const double* x_dev, double* y_dev, int32_t nrhs, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* Solve eq. df_ind (the paper names no linear solver: restarted GMRES)  */
 /* ------------------------------------------------------------------ */

@@ -180,6 +180,21 @@ class Operator:
                                           nrhs, _stream_ptr(stream)))
         return y
 
+    def matvec_noalloc(self, x, y=None, stream=None):
+        """y = A x like matvec, through the allocation-free entry point: the
+        library allocates no device memory for it (n_tet * nrhs <= 2**20).
+        Enqueued on `stream` (default: the library's stream) without a final
+        synchronize; synchronize before reading y."""
+        import torch
+        if not (x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+            raise ValueError("x must be a contiguous CUDA float64 tensor")
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        if y is None:
+            y = torch.empty_like(x)
+        _lib.check(self.ctx._L.bem_matvec_noalloc(self.h, ctypes.c_void_p(x.data_ptr()),
+                                                  ctypes.c_void_p(y.data_ptr()), nrhs, _stream_ptr(stream)))
+        return y
+
     def solve(self, b, tol=1e-8, restart=50, maxit=2000, inner="fp64", max_refine=10, allow_unconverged=False):
         """Host arrays b [n] or [n, nrhs]; returns (w, infos)."""
         b = np.asarray(b, dtype=np.float64)

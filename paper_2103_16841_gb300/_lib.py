@@ -28,7 +28,7 @@ EXPORTS = [
     "bem_mesh_create", "bem_mesh_create_prisms", "bem_mesh_info", "bem_mesh_destroy",
     "bem_operator_create", "bem_operator_stats", "bem_operator_check", "bem_operator_timings", "bem_operator_reassemble", "bem_operator_export_pattern", "bem_operator_pattern_rows",
     "bem_operator_export_dense", "bem_operator_entries", "bem_operator_destroy",
-    "bem_rhs", "bem_matvec", "bem_solve", "bem_solve_device", "bem_inner_potentials",
+    "bem_rhs", "bem_matvec", "bem_matvec_noalloc", "bem_solve", "bem_solve_device", "bem_inner_potentials",
 ]
 
 
@@ -99,6 +99,7 @@ def load(build_if_missing: bool = False):
     L.bem_operator_destroy.restype = None
     L.bem_rhs.argtypes = [VP, ctypes.c_int32, ctypes.c_int32, D, D]
     L.bem_matvec.argtypes = [VP, VP, VP, ctypes.c_int32, VP]
+    L.bem_matvec_noalloc.argtypes = [VP, VP, VP, ctypes.c_int32, VP]
     L.bem_solve.argtypes = [VP, D, D, ctypes.c_int32, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]
     L.bem_solve_device.argtypes = [VP, VP, VP, ctypes.c_int32, ctypes.POINTER(SolveOpts),
                                    ctypes.POINTER(SolveInfo), VP]
