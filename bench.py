@@ -177,7 +177,12 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     prec = args.precision
-    m = inputs.workload_c2(seed=1 + rank) if args.workload == "c2" else inputs.sphere_mesh(2, 8, 2.0, 0.2, seed=3)
+    if args.workload == "c2":
+        m = inputs.workload_c2(seed=1 + rank)
+    elif args.workload == "l3x16":
+        m = inputs.sphere_mesh(3, 16, 4.0, 0.2, seed=1 + rank)
+    else:
+        m = inputs.sphere_mesh(2, 8, 2.0, 0.2, seed=3)
     ctx = stb.Context(local if dist else 0)
     mesh = stb.Mesh.from_spacetime(ctx, m)
     op = stb.Operator(ctx, mesh, prec, store_fp32=True)
@@ -239,6 +244,9 @@ def run_ours(args):
         t_e2e = float(t.item())
     d2h = m.n_tet * 8 + m.n_tet * 8  # rhs vector and density back to the host
 
+    multi = multi_rhs_leg(op, m, args) if args.multi_rhs > 0 else None
+    serving = serving_leg(ctx, args) if (args.serve_requests > 0 and rank == 0) else None
+
     if rank != 0:
         if dist:
             import torch.distributed as tdist
@@ -276,12 +284,122 @@ def run_ours(args):
         "clocks": clk.summary(),
         "roofline": roof,
         "cpu_baseline": cb,
+        "multi_rhs": multi,
+        "serving": serving,
         "peaks": {"hbm_gbs": pk.get("hbm_gbs"), "bf16_tflops": pk.get("bf16_tflops")},
     }
     print(json.dumps(out), flush=True)
     if dist:
         import torch.distributed as tdist
         tdist.destroy_process_group()
+
+
+def multi_rhs_leg(op, m, args):
+    """Many right-hand sides on the assembled operator: the block matvec in
+    FP32 (CUDA cores), TF32 and BF16 (tensor cores) with the values read once
+    per product, and GMRES with inner solves in each arithmetic plus FP64
+    refinement; errors per RHS against the FP32-inner solution refined to
+    1e-10 in FP64."""
+    import torch
+    import paper_2103_16841_gb300 as stb
+    from paper_2103_16841_gb300 import inputs
+    nrhs = args.multi_rhs
+    st = op.stats()
+    n = m.n_tet
+    prm = inputs.pulse_params(nrhs, seed=2)
+    b = op.rhs(stb.DATA_PULSE, prm)
+    x = torch.tensor(np.ascontiguousarray(b.T), device="cuda")
+    out = {"nrhs": nrhs, "pulses": "exp(-((t - x.d - c)/0.25)^2), d seeded unit vectors, c ~ U[1, 2]",
+           "products": {}, "solves": {}}
+    stream = torch.cuda.Stream()
+    for dt in ["fp32", "tf32", "bf16"]:
+        y = op.matvec(x, dtype=dt, stream=stream)          # first call: workspace, autotune
+        reps = 5
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(reps):
+            e0.record(stream)
+            op.matvec(x, y, dtype=dt, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.median(ts))
+        vbytes = st["stored"] * (2 if dt == "bf16" else 4)
+        out["products"][dt] = {"ms": round(ms, 3), "value_bytes": vbytes,
+                               "value_GBps": round(vbytes / (ms / 1e3) / 1e9, 1),
+                               "passes_over_values": math.ceil(nrhs / 4) if dt == "fp32" else math.ceil(nrhs / 64),
+                               "note": "includes the FP64 <-> packed-operand conversions and the caller-order "
+                                       "permutations of bem_matvec_dtype"}
+    ref = None
+    for inner in ["fp32", "tf32", "bf16"]:
+        tol = 1e-10 if inner == "fp32" else 1e-8
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        w, info = op.solve(b, tol=tol, restart=50, maxit=600, inner=inner, max_refine=30, allow_unconverged=True)
+        dt_s = time.perf_counter() - t0
+        rec = {"seconds": round(dt_s, 3), "tol": tol, "converged": int(sum(i["converged"] for i in info)),
+               "iterations_max": int(max(i["iterations"] for i in info)),
+               "refinements": int(info[0]["refinements"]),
+               "rel_residual_max": float(max(i["rel_residual"] for i in info))}
+        if inner == "fp32":
+            ref = w
+        else:
+            err = np.linalg.norm(w - ref, axis=0) / np.linalg.norm(ref, axis=0)
+            rec["rel_error_vs_fp64_refined_per_rhs"] = [float("%.3e" % e) for e in err]
+            rec["rel_error_max"] = float(err.max())
+        out["solves"][inner] = rec
+    return out
+
+
+def serving_leg(ctx, args):
+    """Poisson stream of Dirichlet solves through the continuous-batching
+    server: the mixed-precision form (FP32 quadrature, FP32 inner GMRES, FP64
+    refinement) against the plain FP64 path (FP64 quadrature and GMRES), on
+    the same trace and server settings. Requests are drawn uniformly from
+    icosphere levels x slab counts x right-hand-side counts (T = 4, +-20%
+    jitter, pulse data); latency = submission to completion."""
+    import paper_2103_16841_gb300 as stb
+    from paper_2103_16841_gb300 import inputs
+    rng = np.random.default_rng(4)
+    levels = [1, 2, 3] if args.serve_full else [1, 2]
+    slabs = [8, 16, 32] if args.serve_full else [8, 16]
+    nrhs_set = [1, 4, 16]
+    n = args.serve_requests
+    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, n))
+    reqs = []
+    for k in range(n):
+        lv, sl, nr = int(rng.choice(levels)), int(rng.choice(slabs)), int(rng.choice(nrhs_set))
+        m = inputs.sphere_mesh(lv, sl, 4.0, 0.2, seed=1000 + k)
+        reqs.append((m, inputs.pulse_params(nr, seed=2000 + k), f"L{lv}x{sl}x{nr}"))
+    out = {"requests": n, "poisson_rate_per_s": args.serve_rate, "slots": args.serve_slots,
+           "mix": {"levels": levels, "slabs": slabs, "nrhs": nrhs_set}, "tol": 1e-8, "paths": {}}
+    for name, prec, inner in [("mixed", "mixed", "fp32"), ("fp64", "fp64", "fp64")]:
+        srv = stb.Server(ctx, max_slots=args.serve_slots, precision=prec, inner=inner, tol=1e-8, restart=50,
+                         maxit=3000, max_refine=12)
+        t0 = time.perf_counter()
+        tickets = []
+        for (m, prm, _), ta in zip(reqs, arrivals):
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(srv.submit(m, params=prm))
+        res = srv.wait(tickets, timeout_s=3600)
+        t_end = time.perf_counter()
+        st = srv.stats()
+        srv.close()
+        lat = np.array([res[t]["latency_ms"] for t in tickets])
+        ok = sum(res[t]["status"] == 0 for t in tickets)
+        out["paths"][name] = {
+            "precision": prec, "inner": inner, "completed": int(ok),
+            "solves_per_s": round(float(st["solves_per_s"]), 3),
+            "p50_ms": round(float(np.percentile(lat, 50)), 1), "p99_ms": round(float(np.percentile(lat, 99)), 1),
+            "mean_ms": round(float(lat.mean()), 1), "wall_s": round(t_end - t0, 2),
+            "peak_running": int(st["peak_running"]),
+            "rel_residual_max": float(max(res[t]["rel_residual"] for t in tickets))}
+    mx, fp = out["paths"]["mixed"], out["paths"]["fp64"]
+    out["speedup_solves_per_s"] = round(mx["solves_per_s"] / max(fp["solves_per_s"], 1e-12), 2)
+    return out
 
 
 def load_profile_summary():
@@ -303,8 +421,17 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", dest="cpu_seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="c2", choices=["c2", "l2x8"],
-                    help="l2x8: the level-2 sphere with 8 jittered slabs, for profiler captures only")
+    ap.add_argument("--multi-rhs", dest="multi_rhs", type=int, default=64,
+                    help="right-hand sides of the multi-RHS leg (0: skip)")
+    ap.add_argument("--serve-requests", dest="serve_requests", type=int, default=16,
+                    help="requests of the serving leg (0: skip)")
+    ap.add_argument("--serve-rate", dest="serve_rate", type=float, default=2.0, help="Poisson arrivals per second")
+    ap.add_argument("--serve-slots", dest="serve_slots", type=int, default=4)
+    ap.add_argument("--serve-full", dest="serve_full", action="store_true",
+                    help="draw from levels 1-3 and 8/16/32 slabs (the full serving mix; minutes on the FP64 path)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "l3x16", "l2x8"],
+                    help="l3x16 / l2x8: the level-3 sphere with 16 slabs (T = 4) / the level-2 sphere with "
+                         "8 slabs (T = 2), jittered, for profiler captures only")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -58,8 +58,12 @@ typedef struct bem_operator bem_operator;
  *         quadrature and the closed-form edge terms in single precision. */
 enum { BEM_PREC_FP64 = 0, BEM_PREC_MIXED = 1 };
 
-/* Storage precision of assembled matrix values used by matvec / inner solves. */
-enum { BEM_DTYPE_FP64 = 0, BEM_DTYPE_FP32 = 1 };
+/* Arithmetic of products with the assembled operator:
+ * FP64  FP64 accumulation (of FP64 values, or of FP32 values for MIXED operators);
+ * FP32  FP32 values, x rounded to FP32, FP32 accumulation;
+ * TF32  tensor cores: FP32 values and x rounded to TF32, FP32 accumulation;
+ * BF16  tensor cores: values and x rounded to BF16, FP32 accumulation. */
+enum { BEM_DTYPE_FP64 = 0, BEM_DTYPE_FP32 = 1, BEM_DTYPE_TF32 = 2, BEM_DTYPE_BF16 = 3 };
 
 /* Dirichlet data families (evaluated at space-time points (t, x)):
  *  BEM_DATA_SIN2_UNIFORM: g = sin^2(pi t / 2) for 0 < t < 2, else 0
@@ -199,6 +203,18 @@ bem_status bem_rhs(const bem_operator* op, int32_t kind, int32_t nrhs, const dou
  * enqueued on `stream` (a cudaStream_t; NULL = context stream). */
 bem_status bem_matvec(const bem_operator* op, const double* x_dev, double* y_dev, int32_t nrhs, void* stream);
 
+/* y_dev = A x_dev in the arithmetic `dtype` (BEM_DTYPE_*), same layout as
+ * bem_matvec. TF32 and BF16 run the block matvec on the tensor cores for up
+ * to 64 right-hand sides per pass (the stored values are read once per pass);
+ * FP32, TF32 need the FP32 values (MIXED operators, or store_fp32 = 1); BF16
+ * makes a BF16 copy of the values on first use. The products keep packed
+ * operands in a per-operator workspace (allocated on first use); the first
+ * TF32 / BF16 product of a mesh shape times the candidate launch shapes once
+ * and keeps the fastest for the process (so it synchronizes the stream).
+ * Synchronizes `stream` before returning. */
+bem_status bem_matvec_dtype(const bem_operator* op, const double* x_dev, double* y_dev, int32_t nrhs,
+                            int32_t dtype, void* stream);
+
 /* Allocation-free y_dev = A x_dev (no counterpart in the paper: it exists for
  * callers that cannot let a library allocate device memory while they run,
  * such as a serving loop or runtime that reserves all device memory up front,
@@ -223,7 +239,7 @@ typedef struct {
   double tol;          /* relative residual ||b - A w|| / ||b|| target */
   int32_t restart;     /* GMRES restart length m (1..200) */
   int32_t maxit;       /* max total inner iterations per right-hand side */
-  int32_t inner_dtype; /* BEM_DTYPE_FP64 or BEM_DTYPE_FP32 (then FP64 refinement) */
+  int32_t inner_dtype; /* BEM_DTYPE_FP64, or FP32 / TF32 / BF16 inner solves with FP64 refinement */
   int32_t max_refine;  /* outer refinement steps when inner_dtype != FP64 */
 } bem_solve_opts;
 
@@ -257,6 +273,83 @@ bem_status bem_solve_device(bem_operator* op, const double* b_dev, double* w_dev
  * precision and n_theta as in bem_op_opts. */
 bem_status bem_inner_potentials(bem_context* ctx, int64_t n, const double* x4, const double* tets,
                                 const int32_t* tet_sv, int32_t precision, int32_t n_theta, double* out);
+
+/* ------------------------------------------------------------------ */
+/* Serving: continuous batching of Dirichlet solves (no counterpart in    */
+/* the paper; each request is the problem of eq. df_ind on its own mesh) */
+/* ------------------------------------------------------------------ */
+
+/* A server owns max_slots worker slots, each with its own CUDA stream on the
+ * context's device. Requests queue in arrival order; a free slot takes the
+ * next request, uploads its mesh, builds the sparsity structure, and is then
+ * admitted by HBM footprint: the bytes of the operator's values, row starts,
+ * quadrature scratch and solver workspace are reserved against a pool of
+ * hbm_budget minus the slots' shares (max(hbm_budget / (10 max_slots),
+ * 64 MiB) each, for a request's mesh and sparsity structure); reservations
+ * are granted in arrival order, a request waits in its slot until its
+ * reservation fits, and a request that can never fit (in the pool or in its
+ * slot's share) completes with BEM_ERR_OUT_OF_MEMORY. Slots run
+ * concurrently, so the kernels of different requests overlap on the device;
+ * every request's arithmetic is the same alone and in a mix (its reductions
+ * have a fixed order), so its result does not depend on the other requests. */
+typedef struct bem_server bem_server;
+
+typedef struct {
+  int64_t hbm_budget;    /* bytes the server may hold on the device (0: 90% of free memory) */
+  int32_t max_slots;     /* concurrent requests (1..16) */
+  int32_t precision;     /* BEM_PREC_FP64 or BEM_PREC_MIXED */
+  int32_t inner_dtype;   /* bem_solve_opts.inner_dtype (BEM_DTYPE_FP64 for the plain FP64 path) */
+  int32_t restart, maxit, max_refine;
+  double tol;            /* relative residual target of every solve */
+} bem_server_opts;
+
+typedef struct {         /* one request: a space-time mesh (as bem_mesh_create) and its data */
+  int64_t n_sv;
+  const double* sv_xyz;
+  int64_t n_stv;
+  const int32_t* stv_sv;
+  const double* stv_t;
+  int64_t n_tet;
+  const int32_t* tets;
+  int32_t data_kind;     /* BEM_DATA_* */
+  int32_t nrhs;
+  const double* params;  /* [nrhs][5] for BEM_DATA_PULSE, else NULL */
+} bem_job;
+
+typedef struct {
+  uint64_t ticket;
+  int32_t status;        /* bem_status of the request */
+  int32_t nrhs;
+  int64_t n_tet;
+  const double* w;       /* [nrhs][n_tet] densities (caller order), owned by the server
+                            until bem_server_release(ticket); NULL on failure */
+  int32_t iterations;    /* largest GMRES iteration count over the right-hand sides */
+  int32_t refinements;
+  double rel_residual;   /* largest final relative residual */
+  double queue_ms;       /* submit -> taken by a slot */
+  double latency_ms;     /* submit -> completed */
+  int64_t reserved_bytes;/* HBM reserved at admission */
+} bem_completion;
+
+typedef struct {
+  int64_t submitted, completed, failed, queued, running;
+  int32_t peak_running;  /* most requests admitted at once */
+  int32_t reserved;
+  int64_t peak_reserved_bytes;
+  double solves_per_s;   /* completed / (last completion - first submission) */
+  double p50_ms, p99_ms, mean_ms, max_ms;  /* latency over completed requests */
+} bem_server_stats;
+
+/* Inputs of bem_server_submit are copied; the call never blocks on the GPU. */
+bem_status bem_server_create(bem_context* ctx, const bem_server_opts* opts, bem_server** out);
+bem_status bem_server_submit(bem_server* srv, const bem_job* job, uint64_t* ticket);
+/* Up to max completions not returned before; waits up to timeout_ms (0: no
+ * wait) for at least one. */
+bem_status bem_server_poll(bem_server* srv, bem_completion* out, int32_t max, int32_t* n_out, int64_t timeout_ms);
+bem_status bem_server_release(bem_server* srv, uint64_t ticket);
+bem_status bem_server_stats_get(const bem_server* srv, bem_server_stats* out);
+/* Finishes the queued and running requests, then frees everything. */
+void bem_server_destroy(bem_server* srv);
 
 #ifdef __cplusplus
 }

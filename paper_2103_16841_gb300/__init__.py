@@ -168,16 +168,23 @@ class Operator:
         _lib.check(self.ctx._L.bem_rhs(self.h, int(kind), nrhs, pp, _lib.dptr(b)))
         return b.reshape(nrhs, self.n).T.copy()
 
-    def matvec(self, x, y=None, stream=None):
-        """y = A x for torch CUDA float64 tensors of shape [n] or [nrhs, n]."""
+    def matvec(self, x, y=None, stream=None, dtype=None):
+        """y = A x for torch CUDA float64 tensors of shape [n] or [nrhs, n].
+        dtype None: bem_matvec; "fp64" / "fp32" / "tf32" / "bf16": the
+        arithmetic of bem_matvec_dtype."""
         import torch
         if not (x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
             raise ValueError("x must be a contiguous CUDA float64 tensor")
         nrhs = 1 if x.dim() == 1 else x.shape[0]
         if y is None:
             y = torch.empty_like(x)
-        _lib.check(self.ctx._L.bem_matvec(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
-                                          nrhs, _stream_ptr(stream)))
+        if dtype is None:
+            _lib.check(self.ctx._L.bem_matvec(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                              nrhs, _stream_ptr(stream)))
+        else:
+            _lib.check(self.ctx._L.bem_matvec_dtype(self.h, ctypes.c_void_p(x.data_ptr()),
+                                                    ctypes.c_void_p(y.data_ptr()), nrhs, _lib.DTYPE[dtype],
+                                                    _stream_ptr(stream)))
         return y
 
     def matvec_noalloc(self, x, y=None, stream=None):
@@ -214,6 +221,84 @@ class Operator:
     def close(self):
         if getattr(self, "h", None):
             self.ctx._L.bem_operator_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """bem_server: continuous batching of Dirichlet solves on one device.
+
+    submit() copies a request (space-time mesh + data) and returns its ticket;
+    poll() returns finished requests as dicts with the densities w
+    [nrhs, n_tet] (caller panel order) and their timings."""
+
+    def __init__(self, ctx: Context, hbm_budget=0, max_slots=4, precision="mixed", inner="fp32", tol=1e-8,
+                 restart=50, maxit=2000, max_refine=10):
+        self.ctx = ctx
+        o = _lib.ServerOpts(int(hbm_budget), int(max_slots), _lib.PREC[precision], _lib.DTYPE[inner],
+                            int(restart), int(maxit), int(max_refine), float(tol))
+        h = ctypes.c_void_p()
+        _lib.check(ctx._L.bem_server_create(ctx.h, ctypes.byref(o), ctypes.byref(h)))
+        self.h = h
+
+    def submit(self, m, kind=DATA_PULSE, params=None, nrhs=1):
+        """m: inputs.SpaceTimeMesh; params [nrhs, 5] for DATA_PULSE."""
+        sv = np.ascontiguousarray(m.svert, dtype=np.float64)
+        stv_sv = np.ascontiguousarray(m.stv_sv, dtype=np.int32)
+        stv_t = np.ascontiguousarray(m.stv_t, dtype=np.float64)
+        tets = np.ascontiguousarray(m.tets, dtype=np.int32)
+        prm = None
+        if kind == DATA_PULSE:
+            prm = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 5)
+            nrhs = prm.shape[0]
+        job = _lib.Job(sv.shape[0], _lib.dptr(sv), stv_sv.shape[0], _lib.iptr(stv_sv), _lib.dptr(stv_t),
+                       tets.shape[0], _lib.iptr(tets), int(kind), int(nrhs),
+                       _lib.dptr(prm) if prm is not None else ctypes.POINTER(ctypes.c_double)())
+        t = ctypes.c_uint64()
+        _lib.check(self.ctx._L.bem_server_submit(self.h, ctypes.byref(job), ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, max_items=64, timeout_ms=0):
+        buf = (_lib.Completion * max_items)()
+        n = ctypes.c_int32()
+        _lib.check(self.ctx._L.bem_server_poll(self.h, buf, int(max_items), ctypes.byref(n), int(timeout_ms)))
+        out = []
+        for c in buf[:n.value]:
+            w = None
+            if c.w:
+                w = np.ctypeslib.as_array(c.w, shape=(c.nrhs * c.n_tet,)).copy().reshape(c.nrhs, c.n_tet)
+            out.append({"ticket": int(c.ticket), "status": int(c.status), "w": w, "iterations": int(c.iterations),
+                        "refinements": int(c.refinements), "rel_residual": float(c.rel_residual),
+                        "queue_ms": float(c.queue_ms), "latency_ms": float(c.latency_ms),
+                        "reserved_bytes": int(c.reserved_bytes)})
+            _lib.check(self.ctx._L.bem_server_release(self.h, c.ticket))
+        return out
+
+    def wait(self, tickets, timeout_s=600.0):
+        """Poll until every ticket in `tickets` has completed; returns {ticket: dict}."""
+        import time as _time
+        want, got = set(tickets), {}
+        t_end = _time.time() + timeout_s
+        while want - set(got):
+            if _time.time() > t_end:
+                raise TimeoutError(f"server requests not finished: {sorted(want - set(got))}")
+            for r in self.poll(timeout_ms=200):
+                got[r["ticket"]] = r
+        return got
+
+    def stats(self):
+        st = _lib.ServerStats()
+        _lib.check(self.ctx._L.bem_server_stats_get(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_ if k != "reserved"}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx._L.bem_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -18,7 +18,7 @@ STATUS = {0: "BEM_OK", 1: "BEM_ERR_INVALID_ARG", 2: "BEM_ERR_OUT_OF_MEMORY", 3: 
           4: "BEM_ERR_NOT_CONVERGED", 5: "BEM_ERR_DEVICE_TIMEOUT", 6: "BEM_ERR_UNSUPPORTED",
           7: "BEM_ERR_BAD_MESH", 8: "BEM_ERR_INTERNAL"}
 PREC = {"fp64": 0, "mixed": 1}
-DTYPE = {"fp64": 0, "fp32": 1}
+DTYPE = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 DATA_SIN2_UNIFORM = 0
 DATA_PULSE = 1
 
@@ -28,7 +28,9 @@ EXPORTS = [
     "bem_mesh_create", "bem_mesh_create_prisms", "bem_mesh_info", "bem_mesh_destroy",
     "bem_operator_create", "bem_operator_stats", "bem_operator_check", "bem_operator_timings", "bem_operator_reassemble", "bem_operator_export_pattern", "bem_operator_pattern_rows",
     "bem_operator_export_dense", "bem_operator_entries", "bem_operator_destroy",
-    "bem_rhs", "bem_matvec", "bem_matvec_noalloc", "bem_solve", "bem_solve_device", "bem_inner_potentials",
+    "bem_rhs", "bem_matvec", "bem_matvec_dtype", "bem_matvec_noalloc", "bem_solve", "bem_solve_device", "bem_inner_potentials",
+    "bem_server_create", "bem_server_submit", "bem_server_poll", "bem_server_release", "bem_server_stats_get",
+    "bem_server_destroy",
 ]
 
 
@@ -51,6 +53,35 @@ class SolveOpts(ctypes.Structure):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_int64), ("max_slots", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("inner_dtype", ctypes.c_int32), ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
+                ("max_refine", ctypes.c_int32), ("tol", ctypes.c_double)]
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("n_sv", ctypes.c_int64), ("sv_xyz", ctypes.POINTER(ctypes.c_double)),
+                ("n_stv", ctypes.c_int64), ("stv_sv", ctypes.POINTER(ctypes.c_int32)),
+                ("stv_t", ctypes.POINTER(ctypes.c_double)), ("n_tet", ctypes.c_int64),
+                ("tets", ctypes.POINTER(ctypes.c_int32)), ("data_kind", ctypes.c_int32), ("nrhs", ctypes.c_int32),
+                ("params", ctypes.POINTER(ctypes.c_double))]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("nrhs", ctypes.c_int32),
+                ("n_tet", ctypes.c_int64), ("w", ctypes.POINTER(ctypes.c_double)),
+                ("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32), ("rel_residual", ctypes.c_double),
+                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("reserved_bytes", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("peak_running", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("peak_reserved_bytes", ctypes.c_int64),
+                ("solves_per_s", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -99,14 +130,23 @@ def load(build_if_missing: bool = False):
     L.bem_operator_destroy.restype = None
     L.bem_rhs.argtypes = [VP, ctypes.c_int32, ctypes.c_int32, D, D]
     L.bem_matvec.argtypes = [VP, VP, VP, ctypes.c_int32, VP]
+    L.bem_matvec_dtype.argtypes = [VP, VP, VP, ctypes.c_int32, ctypes.c_int32, VP]
     L.bem_matvec_noalloc.argtypes = [VP, VP, VP, ctypes.c_int32, VP]
     L.bem_solve.argtypes = [VP, D, D, ctypes.c_int32, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]
     L.bem_solve_device.argtypes = [VP, VP, VP, ctypes.c_int32, ctypes.POINTER(SolveOpts),
                                    ctypes.POINTER(SolveInfo), VP]
     L.bem_inner_potentials.argtypes = [VP, ctypes.c_int64, D, D, I32, ctypes.c_int32, ctypes.c_int32, D]
+    L.bem_server_create.argtypes = [VP, ctypes.POINTER(ServerOpts), ctypes.POINTER(VP)]
+    L.bem_server_submit.argtypes = [VP, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_uint64)]
+    L.bem_server_poll.argtypes = [VP, ctypes.POINTER(Completion), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.c_int64]
+    L.bem_server_release.argtypes = [VP, ctypes.c_uint64]
+    L.bem_server_stats_get.argtypes = [VP, ctypes.POINTER(ServerStats)]
+    L.bem_server_destroy.argtypes = [VP]
+    L.bem_server_destroy.restype = None
     for name in EXPORTS:
         if name not in ("bem_context_destroy", "bem_mesh_destroy", "bem_operator_destroy", "bem_last_error",
-                        "bem_version"):
+                        "bem_version", "bem_server_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L

@@ -384,12 +384,13 @@ bem_status assemble(bem_operator* op, cudaStream_t s, bool first) {
   }
   if (first) {
     op->nstored = vo; op->nrows_stored = ro; op->nnz = nnz; op->nblocks = nblk;
+    int grid = quad_grid(op);
+    op->tmp_len = std::max<int64_t>((int64_t)grid * m->max_col_surf * m->max_col_tets, 2 * m->n_tet * 8);
+    if (op->admit) TRY(op->admit(op));
     // mixed-precision values carry FP32 accuracy: FP32 storage only
     if (op->opts.precision == BEM_PREC_FP64) TRY(dalloc(&op->d_val, (size_t)vo));
     if (op->opts.store_fp32 || op->opts.precision == BEM_PREC_MIXED) TRY(dalloc(&op->d_val32, (size_t)vo));
     TRY(dalloc(&op->d_rs, (size_t)ro));
-    int grid = quad_grid(op);
-    op->tmp_len = std::max<int64_t>((int64_t)grid * m->max_col_surf * m->max_col_tets, 2 * m->n_tet * 8);
     TRY(dalloc(&op->d_tmp, (size_t)op->tmp_len));
   } else if (vo != op->nstored || nnz != op->nnz) {
     set_error("reassembly changed the sparsity structure");
@@ -416,9 +417,23 @@ bem_status assemble(bem_operator* op, cudaStream_t s, bool first) {
 
 }  // namespace
 
+int64_t stbem::operator_value_bytes(const bem_operator* op) {
+  int64_t b = 0;
+  if (op->opts.precision == BEM_PREC_FP64) b += 8 * op->nstored;
+  if (op->opts.store_fp32 || op->opts.precision == BEM_PREC_MIXED) b += 4 * op->nstored;
+  return b + 4 * op->nrows_stored + 8 * op->tmp_len;
+}
+
 extern "C" {
 
 bem_status bem_operator_create(bem_context* ctx, const bem_mesh* mesh, const bem_op_opts* opts, bem_operator** out) {
+  return stbem::operator_create(ctx, mesh, opts, nullptr, out);
+}
+
+}  // extern "C"
+
+bem_status stbem::operator_create(bem_context* ctx, const bem_mesh* mesh, const bem_op_opts* opts,
+                                  std::function<bem_status(const bem_operator*)> admit, bem_operator** out) {
   if (!ctx || !mesh || !out) { set_error("bem_operator_create: invalid argument"); return BEM_ERR_INVALID_ARG; }
   *out = nullptr;
   bem_op_opts o{};
@@ -436,6 +451,7 @@ bem_status bem_operator_create(bem_context* ctx, const bem_mesh* mesh, const bem
   std::unique_ptr<bem_operator> op(new bem_operator());
   op->ctx = ctx; op->mesh = mesh; op->opts = o;
   op->mq = o.m_q; op->nq = o.m_q * o.m_q; op->n_theta = o.n_theta;
+  op->admit = std::move(admit);
   const int64_t nb = mesh->n_col * mesh->n_col;
   TRY(dalloc(&op->d_pts, (size_t)mesh->n_surf * op->nq * 4));
   TRY(dalloc(&op->d_pts_trange, (size_t)mesh->n_surf * 2));
@@ -454,9 +470,12 @@ bem_status bem_operator_create(bem_context* ctx, const bem_mesh* mesh, const bem
     st = BEM_ERR_INTERNAL;
   }
   if (st != BEM_OK) { bem_operator_destroy(op.release()); return st; }
+  op->admit = nullptr;
   *out = op.release();
   return BEM_OK;
 }
+
+extern "C" {
 
 bem_status bem_operator_check(const bem_operator* op, int64_t* n_nonfinite, double* max_abs) {
   if (!op) { set_error("null operator"); return BEM_ERR_INVALID_ARG; }
@@ -493,6 +512,7 @@ void bem_operator_destroy(bem_operator* op) {
   cudaFree(op->d_pts); cudaFree(op->d_pts_trange); cudaFree(op->d_bw); cudaFree(op->d_bnnz);
   cudaFree(op->d_boff); cudaFree(op->d_rsoff); cudaFree(op->d_rs); cudaFree(op->d_val);
   cudaFree(op->d_val32); cudaFree(op->d_tmp); cudaFree(op->d_counter);
+  cudaFree(op->d_val16); cudaFree(op->d_ws);
   delete op;
 }
 
@@ -673,6 +693,24 @@ bem_status bem_matvec(const bem_operator* op, const double* x_dev, double* y_dev
   return BEM_OK;
 }
 
+bem_status bem_matvec_dtype(const bem_operator* op, const double* x_dev, double* y_dev, int32_t nrhs, int32_t dtype,
+                            void* stream) {
+  if (!op || !x_dev || !y_dev || nrhs <= 0 || dtype < BEM_DTYPE_FP64 || dtype > BEM_DTYPE_BF16) {
+    set_error("bem_matvec_dtype: invalid argument");
+    return BEM_ERR_INVALID_ARG;
+  }
+  const bem_mesh* m = op->mesh;
+  cudaStream_t s = pick(op->ctx, stream);
+  const int64_t nn = m->n_tet * nrhs;
+  DevBuf<double> xi, yi;
+  TRY(xi.alloc(nn)); TRY(yi.alloc(nn));
+  TRY(permute(m->d_perm, x_dev, xi.p, m->n_tet, nrhs, true, s));
+  TRY(op_matvec(op, xi.p, yi.p, nrhs, dtype, s));
+  TRY(permute(m->d_perm, yi.p, y_dev, m->n_tet, nrhs, false, s));
+  STBEM_CUDA(cudaStreamSynchronize(s));
+  return BEM_OK;
+}
+
 bem_status bem_solve_device(bem_operator* op, const double* b_dev, double* w_dev, int32_t nrhs,
                             const bem_solve_opts* opts, bem_solve_info* info, void* stream) {
   if (!op || !b_dev || !w_dev || nrhs <= 0) { set_error("bem_solve: invalid argument"); return BEM_ERR_INVALID_ARG; }
@@ -682,8 +720,12 @@ bem_status bem_solve_device(bem_operator* op, const double* b_dev, double* w_dev
     set_error("bem_solve: bad options");
     return BEM_ERR_INVALID_ARG;
   }
-  if (o.inner_dtype == BEM_DTYPE_FP32 && !op->d_val32 && op->d_val) {
-    set_error("FP32 inner solves need store_fp32 = 1");
+  if (o.inner_dtype < BEM_DTYPE_FP64 || o.inner_dtype > BEM_DTYPE_BF16) {
+    set_error("bem_solve: unknown inner_dtype");
+    return BEM_ERR_INVALID_ARG;
+  }
+  if ((o.inner_dtype == BEM_DTYPE_FP32 || o.inner_dtype == BEM_DTYPE_TF32) && !op->d_val32) {
+    set_error("FP32 / TF32 inner solves need store_fp32 = 1");
     return BEM_ERR_INVALID_ARG;
   }
   const bem_mesh* m = op->mesh;

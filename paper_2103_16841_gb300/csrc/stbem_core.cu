@@ -658,72 +658,6 @@ bem_status op_quadrature(bem_operator* op, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Matrix-vector product over the block-banded storage.
-// One CTA per test column I; G groups of R_I threads split the trial columns
-// J (g, g+G, ...), each thread owns one row; per block the band values are
-// read column-major (consecutive rows -> consecutive addresses).
-// ---------------------------------------------------------------------------
-template <typename V>
-__global__ void k_matvec(int64_t n_col, const int32_t* col_tet_begin, const int32_t* bw, const int64_t* boff,
-                         const int64_t* rsoff, const int32_t* rs, const V* val, const double* x, double* y,
-                         int64_t n_tet, int nrhs, int groups) {
-  extern __shared__ double red[];
-  const int64_t I = blockIdx.x;
-  const int t0 = col_tet_begin[I], nt = col_tet_begin[I + 1] - t0;
-  const int rows_pad = blockDim.x / groups;
-  const int g = threadIdx.x / rows_pad, r = threadIdx.x % rows_pad;
-  for (int rh = 0; rh < nrhs; ++rh) {
-    const double* xr = x + (int64_t)rh * n_tet;
-    double acc = 0.0;
-    if (r < nt) {
-      for (int64_t J = g; J < n_col; J += groups) {
-        int64_t b = I * n_col + J;
-        int W = bw[b];
-        if (W == 0) continue;
-        int64_t vo = boff[b];
-        int start = rs[rsoff[b] + r];
-        int jend = col_tet_begin[J + 1];
-        const V* v = val + vo + r;
-        for (int w = 0; w < W; ++w) {
-          int j = start + w;
-          j = j < jend ? j : jend - 1;
-          acc += (double)v[(int64_t)w * nt] * xr[j];
-        }
-      }
-    }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    if (g == 0 && r < nt) {
-      double s = 0.0;
-      for (int k = 0; k < groups; ++k) s += red[k * rows_pad + r];
-      y[(int64_t)rh * n_tet + t0 + r] = s;
-    }
-    __syncthreads();
-  }
-}
-
-bem_status op_matvec(const bem_operator* op, const double* x, double* y, int nrhs, bool fp32, cudaStream_t s) {
-  const bem_mesh* m = op->mesh;
-  if (!op->d_val) fp32 = true;  // mixed-precision operators keep FP32 values only
-  int rows_pad = ((m->max_col_tets + 31) / 32) * 32;
-  int groups = std::max(1, std::min(8, 512 / rows_pad));
-  int threads = rows_pad * groups;
-  size_t smem = sizeof(double) * threads;
-  if (fp32) {
-    if (!op->d_val32) { set_error("operator has no FP32 values (store_fp32 = 0)"); return BEM_ERR_INVALID_ARG; }
-    k_matvec<float><<<(unsigned)m->n_col, threads, smem, s>>>(m->n_col, m->d_col_tet_begin, op->d_bw, op->d_boff,
-                                                               op->d_rsoff, op->d_rs, op->d_val32, x, y, m->n_tet,
-                                                               nrhs, groups);
-  } else {
-    k_matvec<double><<<(unsigned)m->n_col, threads, smem, s>>>(m->n_col, m->d_col_tet_begin, op->d_bw, op->d_boff,
-                                                                op->d_rsoff, op->d_rs, op->d_val, x, y, m->n_tet,
-                                                                nrhs, groups);
-  }
-  STBEM_CUDA(cudaGetLastError());
-  return BEM_OK;
-}
-
-// ---------------------------------------------------------------------------
 // Value scan: non-finite count and largest magnitude
 // ---------------------------------------------------------------------------
 template <typename V>

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -89,6 +90,13 @@ struct bem_operator {
   // quadrature scratch
   double* d_tmp = nullptr;
   int64_t tmp_len = 0;
+  // made on first use by the products (an operator is used by one host thread at a time)
+  mutable uint16_t* d_val16 = nullptr;  // BF16 copy of the values
+  mutable float* d_ws = nullptr;        // packed operands of the FP32 / tensor-core products
+  mutable int64_t ws_len = 0;
+  // optional admission hook, called once the sparsity structure is known
+  // (nstored, nrows_stored, tmp_len set) and before the value arrays are allocated
+  std::function<bem_status(const bem_operator*)> admit;
 };
 
 namespace stbem {
@@ -99,7 +107,16 @@ bem_status mesh_device_geometry(bem_mesh* m, const double* d_sv_xyz, const int32
 bem_status op_outer_points(bem_operator* op, cudaStream_t s);
 bem_status op_pattern(bem_operator* op, cudaStream_t s);
 bem_status op_quadrature(bem_operator* op, cudaStream_t s);
-bem_status op_matvec(const bem_operator* op, const double* x, double* y, int nrhs, bool fp32, cudaStream_t s);
+// operator creation with an admission hook (see bem_operator::admit)
+bem_status operator_create(bem_context* ctx, const bem_mesh* mesh, const bem_op_opts* opts,
+                           std::function<bem_status(const bem_operator*)> admit, bem_operator** out);
+// bytes held by an operator's value arrays, row starts and quadrature scratch
+int64_t operator_value_bytes(const bem_operator* op);
+// arithmetic of a product (values equal to BEM_DTYPE_*)
+enum { MV_FP64 = 0, MV_FP32 = 1, MV_TF32 = 2, MV_BF16 = 3 };
+bem_status op_matvec(const bem_operator* op, const double* x, double* y, int nrhs, int arith, cudaStream_t s);
+// warps per strip the SpMM autotuner picked for this operator's shape (0: not yet tuned)
+int spmm_tuned_ws(const bem_operator* op, int nrhs, int arith);
 bem_status op_rhs(const bem_operator* op, int kind, int nrhs, const double* d_params, double* d_b, cudaStream_t s);
 bem_status op_value_scan(const bem_operator* op, int64_t* nbad, double* maxabs, cudaStream_t s);
 bem_status op_entries(const bem_operator* op, int64_t n, const int32_t* d_ij, double* d_out, cudaStream_t s);

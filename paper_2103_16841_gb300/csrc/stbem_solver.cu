@@ -82,10 +82,10 @@ static bem_status norms(const double* v, int64_t n, int nrhs, double* d_tmp, std
   return BEM_OK;
 }
 
-// GMRES(m) on A (fp32: the FP32 copy of the values), solving A x = b for all
+// GMRES(m) on A with products in the arithmetic `arith` (MV_*), solving A x = b for all
 // columns; x holds the initial guess and the result. Returns per-rhs
 // iterations and relative residual estimates.
-static bem_status gmres_inner(const bem_operator* op, bool fp32, const double* b, double* x, int nrhs, double tol,
+static bem_status gmres_inner(const bem_operator* op, int arith, const double* b, double* x, int nrhs, double tol,
                               int m, int maxit, std::vector<int>& iters, std::vector<double>& relres,
                               std::vector<int>& conv, cudaStream_t s) {
   const int64_t n = op->mesh->n_tet;
@@ -107,7 +107,7 @@ static bem_status gmres_inner(const bem_operator* op, bool fp32, const double* b
   int total = 0;
   while (total < maxit) {
     // r = b - A x
-    st = op_matvec(op, x, w.p, nrhs, fp32, s);
+    st = op_matvec(op, x, w.p, nrhs, arith, s);
     if (st != BEM_OK) return st;
     k_sub<<<nb(nn), 256, 0, s>>>(b, w.p, r.p, nn);
     std::vector<double> beta;
@@ -132,7 +132,7 @@ static bem_status gmres_inner(const bem_operator* op, bool fp32, const double* b
     int j = 0;
     for (; j < m && total < maxit; ++j, ++total) {
       double* Vj = V.p + (int64_t)j * nn;
-      st = op_matvec(op, Vj, w.p, nrhs, fp32, s);
+      st = op_matvec(op, Vj, w.p, nrhs, arith, s);
       if (st != BEM_OK) return st;
       // two classical Gram-Schmidt passes
       for (int pass = 0; pass < 2; ++pass) {
@@ -203,7 +203,7 @@ static bem_status gmres_inner(const bem_operator* op, bool fp32, const double* b
     if (kmax == 0) break;
   }
   // final true residual
-  st = op_matvec(op, x, w.p, nrhs, fp32, s);
+  st = op_matvec(op, x, w.p, nrhs, arith, s);
   if (st != BEM_OK) return st;
   k_sub<<<nb(nn), 256, 0, s>>>(b, w.p, r.p, nn);
   std::vector<double> fin;
@@ -227,7 +227,7 @@ bem_status gmres_solve(bem_operator* op, const double* d_b, double* d_x, int nrh
   int refinements = 0;
   std::vector<int> tot_iters(nrhs, 0);
   if (o->inner_dtype == BEM_DTYPE_FP64) {
-    st = gmres_inner(op, false, d_b, d_x, nrhs, o->tol, o->restart, o->maxit, iters, rel, conv, s);
+    st = gmres_inner(op, MV_FP64, d_b, d_x, nrhs, o->tol, o->restart, o->maxit, iters, rel, conv, s);
     if (st != BEM_OK) return st;
     tot_iters = iters;
   } else {
@@ -243,9 +243,12 @@ bem_status gmres_solve(bem_operator* op, const double* d_b, double* d_x, int nrh
     if (st != BEM_OK) return st;
     rel.assign(nrhs, 1.0);
     conv.assign(nrhs, 0);
-    double inner_tol = std::max(o->tol, 1e-5);
+    // inner tolerance near the unit roundoff of the inner arithmetic: each
+    // refinement step contracts the error by about cond(A) * u_inner anyway
+    const double u_floor = o->inner_dtype == BEM_DTYPE_BF16 ? 1e-2 : o->inner_dtype == BEM_DTYPE_TF32 ? 1e-3 : 1e-5;
+    double inner_tol = std::max(o->tol, u_floor);
     for (int it = 0; it <= std::max(0, o->max_refine); ++it) {
-      st = op_matvec(op, d_x, Ax.p, nrhs, false, s);
+      st = op_matvec(op, d_x, Ax.p, nrhs, MV_FP64, s);
       if (st != BEM_OK) return st;
       k_sub<<<nb(nn), 256, 0, s>>>(d_b, Ax.p, r.p, nn);
       std::vector<double> rn;
@@ -261,7 +264,7 @@ bem_status gmres_solve(bem_operator* op, const double* d_b, double* d_x, int nrh
       STBEM_CUDA(cudaMemsetAsync(dx.p, 0, sizeof(double) * nn, s));
       std::vector<int> ci;
       std::vector<double> ri;
-      st = gmres_inner(op, true, r.p, dx.p, nrhs, inner_tol, o->restart, o->maxit, iters, ri, ci, s);
+      st = gmres_inner(op, o->inner_dtype, r.p, dx.p, nrhs, inner_tol, o->restart, o->maxit, iters, ri, ci, s);
       if (st != BEM_OK) return st;
       for (int k = 0; k < nrhs; ++k) tot_iters[k] += iters[k];
       k_axpy<<<nb(nn), 256, 0, s>>>(1.0, dx.p, d_x, nn);

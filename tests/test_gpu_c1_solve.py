@@ -53,3 +53,20 @@ def test_c1_mixed_refined_vs_oracle_lu(c1_lu):
     rel = np.linalg.norm(w - w_ref) / np.linalg.norm(w_ref)
     print("C1 mixed + refinement vs oracle LU: %.3e" % rel)
     assert rel <= 1e-6
+
+
+@pytest.mark.parametrize("inner", ["tf32", "bf16"])
+def test_c1_tensor_core_inner_solves_vs_oracle_lu(c1_lu, inner):
+    """Inner GMRES with tensor-core products (TF32 or BF16 values and
+    vectors, FP32 accumulation) inside the FP64 refinement reaches the same
+    solution as FP32 inner solves: the bar of the mixed form, <= 1e-6."""
+    import paper_2103_16841_gb300 as stb
+    ctx, m, mesh, w_ref = c1_lu
+    op = stb.Operator(ctx, mesh, "mixed")
+    w, info = op.solve(op.rhs(stb.DATA_SIN2_UNIFORM)[:, 0], tol=1e-12, restart=100, maxit=2000,
+                       inner=inner, max_refine=40)
+    assert info[0]["converged"]
+    rel = np.linalg.norm(w - w_ref) / np.linalg.norm(w_ref)
+    print("C1 mixed, %s inner + FP64 refinement (%d refinements) vs oracle LU: %.3e"
+          % (inner, info[0]["refinements"], rel))
+    assert rel <= 1e-6
