@@ -275,6 +275,32 @@ bem_status bem_inner_potentials(bem_context* ctx, int64_t n, const double* x4, c
                                 const int32_t* tet_sv, int32_t precision, int32_t n_theta, double* out);
 
 /* ------------------------------------------------------------------ */
+/* Batches of small scatterers (no counterpart in the paper: many         */
+/* independent problems of eq. df_ind solved together)                  */
+/* ------------------------------------------------------------------ */
+
+/* Assembles the operators of n meshes (all on ctx's device, opts as for
+ * bem_operator_create, one precision for all) with one persistent launch per
+ * pass over the blocks of every operator. The meshes must outlive the batch. */
+typedef struct bem_batch bem_batch;
+bem_status bem_batch_create(bem_context* ctx, int32_t n, const bem_mesh* const* meshes, const bem_op_opts* opts,
+                            bem_batch** out);
+bem_status bem_batch_stats(const bem_batch* batch, int32_t* n_ops, int64_t* n_tet_total, int64_t* nnz,
+                           double* assemble_ms);
+/* Solves every operator's problem for its own right-hand sides: nrhs[i]
+ * pulses for operator i (params: the [nrhs[i]][5] rows of all operators
+ * concatenated; NULL for SIN2_UNIFORM). The block-diagonal system runs as one
+ * set of GMRES launches (each (scatterer, right-hand side) an independent
+ * Krylov column; blocks of Arnoldi steps captured as CUDA graphs, the active
+ * columns checked between graph launches); opts->inner_dtype FP64 or FP32
+ * (then FP64 refinement). w (host): the [nrhs[i]][n_tet_i] densities of the
+ * operators concatenated, caller panel order; info: one per right-hand side
+ * in the same order (may be NULL). */
+bem_status bem_batch_solve(bem_batch* batch, int32_t data_kind, const int32_t* nrhs, const double* params,
+                           const bem_solve_opts* opts, double* w, bem_solve_info* info);
+void bem_batch_destroy(bem_batch* batch);
+
+/* ------------------------------------------------------------------ */
 /* Serving: continuous batching of Dirichlet solves (no counterpart in    */
 /* the paper; each request is the problem of eq. df_ind on its own mesh) */
 /* ------------------------------------------------------------------ */

@@ -230,6 +230,70 @@ class Operator:
             pass
 
 
+class Batch:
+    """bem_batch: the operators of many small meshes assembled by one
+    persistent launch per pass and solved as one block-diagonal system."""
+
+    def __init__(self, ctx: Context, meshes, precision="mixed", m_q=3, n_theta=0, store_fp32=True):
+        self.ctx = ctx
+        self.meshes = list(meshes)          # the meshes must outlive the batch
+        o = _lib.OpOpts(_lib.PREC[precision], int(m_q), int(n_theta), int(bool(store_fp32)))
+        arr = (ctypes.c_void_p * len(self.meshes))(*[mm.h.value for mm in self.meshes])
+        h = ctypes.c_void_p()
+        _lib.check(ctx._L.bem_batch_create(ctx.h, len(self.meshes), arr, ctypes.byref(o), ctypes.byref(h)))
+        self.h = h
+        self.n_tet = [Mesh_info(ctx, mm)[0] for mm in self.meshes]
+
+    def stats(self):
+        n = ctypes.c_int32()
+        nt, nnz = ctypes.c_int64(), ctypes.c_int64()
+        ms = ctypes.c_double()
+        _lib.check(self.ctx._L.bem_batch_stats(self.h, ctypes.byref(n), ctypes.byref(nt), ctypes.byref(nnz),
+                                               ctypes.byref(ms)))
+        return {"n_ops": n.value, "n_tet": nt.value, "nnz": nnz.value, "assemble_ms": ms.value}
+
+    def solve(self, params_list, tol=1e-8, restart=50, maxit=2000, inner="fp32", max_refine=10,
+              allow_unconverged=False):
+        """params_list: one [nrhs_i, 5] pulse array per mesh. Returns (list of
+        w_i [n_tet_i, nrhs_i], list of per-RHS info lists)."""
+        nrhs = np.array([np.asarray(p).reshape(-1, 5).shape[0] for p in params_list], dtype=np.int32)
+        prm = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.float64).reshape(-1, 5)
+                                                   for p in params_list]))
+        total = int(sum(n * k for n, k in zip(self.n_tet, nrhs)))
+        w = np.zeros(total)
+        infos = (_lib.SolveInfo * int(nrhs.sum()))()
+        o = _lib.SolveOpts(float(tol), int(restart), int(maxit), _lib.DTYPE[inner], int(max_refine))
+        st = self.ctx._L.bem_batch_solve(self.h, DATA_PULSE, _lib.iptr(nrhs), _lib.dptr(prm), ctypes.byref(o),
+                                         _lib.dptr(w), infos)
+        _lib.check(st, allow=(4,) if allow_unconverged else ())
+        ws, inf, off, row = [], [], 0, 0
+        for n, k in zip(self.n_tet, nrhs):
+            ws.append(w[off:off + n * k].reshape(k, n).T.copy())
+            inf.append([{"iterations": infos[row + q].iterations, "refinements": infos[row + q].refinements,
+                         "converged": bool(infos[row + q].converged), "rel_residual": infos[row + q].rel_residual,
+                         "solve_ms": infos[row + q].solve_ms} for q in range(k)])
+            off += n * k
+            row += k
+        return ws, inf
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx._L.bem_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def Mesh_info(ctx, mesh):
+    nt, nc, ns = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _lib.check(ctx._L.bem_mesh_info(mesh.h, ctypes.byref(nt), ctypes.byref(nc), ctypes.byref(ns)))
+    return nt.value, nc.value, ns.value
+
+
 class Server:
     """bem_server: continuous batching of Dirichlet solves on one device.
 

@@ -29,6 +29,7 @@ EXPORTS = [
     "bem_operator_create", "bem_operator_stats", "bem_operator_check", "bem_operator_timings", "bem_operator_reassemble", "bem_operator_export_pattern", "bem_operator_pattern_rows",
     "bem_operator_export_dense", "bem_operator_entries", "bem_operator_destroy",
     "bem_rhs", "bem_matvec", "bem_matvec_dtype", "bem_matvec_noalloc", "bem_solve", "bem_solve_device", "bem_inner_potentials",
+    "bem_batch_create", "bem_batch_stats", "bem_batch_solve", "bem_batch_destroy",
     "bem_server_create", "bem_server_submit", "bem_server_poll", "bem_server_release", "bem_server_stats_get",
     "bem_server_destroy",
 ]
@@ -136,6 +137,11 @@ def load(build_if_missing: bool = False):
     L.bem_solve_device.argtypes = [VP, VP, VP, ctypes.c_int32, ctypes.POINTER(SolveOpts),
                                    ctypes.POINTER(SolveInfo), VP]
     L.bem_inner_potentials.argtypes = [VP, ctypes.c_int64, D, D, I32, ctypes.c_int32, ctypes.c_int32, D]
+    L.bem_batch_create.argtypes = [VP, ctypes.c_int32, ctypes.POINTER(VP), ctypes.POINTER(OpOpts), ctypes.POINTER(VP)]
+    L.bem_batch_stats.argtypes = [VP, ctypes.POINTER(ctypes.c_int32), I64, I64, D]
+    L.bem_batch_solve.argtypes = [VP, ctypes.c_int32, I32, D, ctypes.POINTER(SolveOpts), D, ctypes.POINTER(SolveInfo)]
+    L.bem_batch_destroy.argtypes = [VP]
+    L.bem_batch_destroy.restype = None
     L.bem_server_create.argtypes = [VP, ctypes.POINTER(ServerOpts), ctypes.POINTER(VP)]
     L.bem_server_submit.argtypes = [VP, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_uint64)]
     L.bem_server_poll.argtypes = [VP, ctypes.POINTER(Completion), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
@@ -146,7 +152,7 @@ def load(build_if_missing: bool = False):
     L.bem_server_destroy.restype = None
     for name in EXPORTS:
         if name not in ("bem_context_destroy", "bem_mesh_destroy", "bem_operator_destroy", "bem_last_error",
-                        "bem_version", "bem_server_destroy"):
+                        "bem_version", "bem_server_destroy", "bem_batch_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L

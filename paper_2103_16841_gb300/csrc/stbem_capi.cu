@@ -345,6 +345,81 @@ void bem_mesh_destroy(bem_mesh* m) {
 
 }  // extern "C"
 
+bem_status stbem::op_layout(bem_operator* op, const int32_t* bw, const int64_t* bnnz, bool first, bool own_scratch,
+                           cudaStream_t s) {
+  const bem_mesh* m = op->mesh;
+  const int64_t nb = m->n_col * m->n_col;
+  std::vector<int64_t> boff(nb), rsoff(nb);
+  int64_t vo = 0, ro = 0, nnz = 0, nblk = 0;
+  int wmax = 0;
+  for (int64_t I = 0; I < m->n_col; ++I) {
+    int R = m->col_tet_begin[I + 1] - m->col_tet_begin[I];
+    for (int64_t J = 0; J < m->n_col; ++J) {
+      int64_t b = I * m->n_col + J;
+      boff[b] = vo;
+      rsoff[b] = ro;
+      if (bw[b] > 0) {
+        vo += (int64_t)R * bw[b];
+        ro += R;
+        ++nblk;
+        wmax = std::max(wmax, bw[b]);
+      }
+      nnz += bnnz[b];
+    }
+  }
+  if (first) {
+    op->nstored = vo; op->nrows_stored = ro; op->nnz = nnz; op->nblocks = nblk;
+    op->max_bw = wmax;
+    if (own_scratch) {
+      int grid = quad_grid(op);
+      op->tmp_len = std::max<int64_t>((int64_t)grid * m->max_col_surf * m->max_col_tets, 2 * m->n_tet * 8);
+    } else {
+      op->tmp_len = 0;
+    }
+    if (op->admit) TRY(op->admit(op));
+    // mixed-precision values carry FP32 accuracy: FP32 storage only
+    if (op->opts.precision == BEM_PREC_FP64) TRY(dalloc(&op->d_val, (size_t)vo));
+    if (op->opts.store_fp32 || op->opts.precision == BEM_PREC_MIXED) TRY(dalloc(&op->d_val32, (size_t)vo));
+    TRY(dalloc(&op->d_rs, (size_t)ro));
+    if (own_scratch) TRY(dalloc(&op->d_tmp, (size_t)op->tmp_len));
+  } else if (vo != op->nstored || nnz != op->nnz) {
+    set_error("reassembly changed the sparsity structure");
+    return BEM_ERR_INTERNAL;
+  }
+  STBEM_CUDA(cudaMemcpyAsync(op->d_boff, boff.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, s));
+  STBEM_CUDA(cudaMemcpyAsync(op->d_rsoff, rsoff.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, s));
+  // the host offsets must stay alive until the copies are done
+  STBEM_CUDA(cudaStreamSynchronize(s));
+  return BEM_OK;
+}
+
+bem_status stbem::op_structure_alloc(bem_context* ctx, const bem_mesh* mesh, const bem_op_opts* opts,
+                                     std::unique_ptr<bem_operator>& op) {
+  bem_op_opts o{};
+  o.precision = BEM_PREC_FP64; o.m_q = 3; o.n_theta = 0; o.store_fp32 = 1;
+  if (opts) o = *opts;
+  if (o.precision != BEM_PREC_FP64 && o.precision != BEM_PREC_MIXED) {
+    set_error("unknown precision"); return BEM_ERR_INVALID_ARG;
+  }
+  if (o.m_q < 1 || o.m_q > 4) { set_error("m_q must be in 1..4"); return BEM_ERR_UNSUPPORTED; }
+  if (o.n_theta != 0 && (o.n_theta < 4 || o.n_theta > MAX_NTHETA)) {
+    set_error("n_theta must be 0 or in 4..32");
+    return BEM_ERR_INVALID_ARG;
+  }
+  op.reset(new bem_operator());
+  op->ctx = ctx; op->mesh = mesh; op->opts = o;
+  op->mq = o.m_q; op->nq = o.m_q * o.m_q; op->n_theta = o.n_theta;
+  const int64_t nb = mesh->n_col * mesh->n_col;
+  TRY(dalloc(&op->d_pts, (size_t)mesh->n_surf * op->nq * 4));
+  TRY(dalloc(&op->d_pts_trange, (size_t)mesh->n_surf * 2));
+  TRY(dalloc(&op->d_bw, (size_t)nb));
+  TRY(dalloc(&op->d_bnnz, (size_t)nb));
+  TRY(dalloc(&op->d_boff, (size_t)nb));
+  TRY(dalloc(&op->d_rsoff, (size_t)nb));
+  TRY(dalloc(&op->d_counter, 4));
+  return BEM_OK;
+}
+
 namespace {
 
 bem_status assemble(bem_operator* op, cudaStream_t s, bool first) {
@@ -366,38 +441,7 @@ bem_status assemble(bem_operator* op, cudaStream_t s, bool first) {
   STBEM_CUDA(cudaMemcpyAsync(bw.data(), op->d_bw, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, s));
   STBEM_CUDA(cudaMemcpyAsync(bnnz.data(), op->d_bnnz, sizeof(int64_t) * nb, cudaMemcpyDeviceToHost, s));
   STBEM_CUDA(cudaStreamSynchronize(s));
-  std::vector<int64_t> boff(nb), rsoff(nb);
-  int64_t vo = 0, ro = 0, nnz = 0, nblk = 0;
-  for (int64_t I = 0; I < m->n_col; ++I) {
-    int R = m->col_tet_begin[I + 1] - m->col_tet_begin[I];
-    for (int64_t J = 0; J < m->n_col; ++J) {
-      int64_t b = I * m->n_col + J;
-      boff[b] = vo;
-      rsoff[b] = ro;
-      if (bw[b] > 0) {
-        vo += (int64_t)R * bw[b];
-        ro += R;
-        ++nblk;
-      }
-      nnz += bnnz[b];
-    }
-  }
-  if (first) {
-    op->nstored = vo; op->nrows_stored = ro; op->nnz = nnz; op->nblocks = nblk;
-    int grid = quad_grid(op);
-    op->tmp_len = std::max<int64_t>((int64_t)grid * m->max_col_surf * m->max_col_tets, 2 * m->n_tet * 8);
-    if (op->admit) TRY(op->admit(op));
-    // mixed-precision values carry FP32 accuracy: FP32 storage only
-    if (op->opts.precision == BEM_PREC_FP64) TRY(dalloc(&op->d_val, (size_t)vo));
-    if (op->opts.store_fp32 || op->opts.precision == BEM_PREC_MIXED) TRY(dalloc(&op->d_val32, (size_t)vo));
-    TRY(dalloc(&op->d_rs, (size_t)ro));
-    TRY(dalloc(&op->d_tmp, (size_t)op->tmp_len));
-  } else if (vo != op->nstored || nnz != op->nnz) {
-    set_error("reassembly changed the sparsity structure");
-    return BEM_ERR_INTERNAL;
-  }
-  STBEM_CUDA(cudaMemcpyAsync(op->d_boff, boff.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, s));
-  STBEM_CUDA(cudaMemcpyAsync(op->d_rsoff, rsoff.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, s));
+  TRY(op_layout(op, bw.data(), bnnz.data(), first, true, s));
   STBEM_CUDA(cudaEventRecord(ec, s));
   TRY(op_quadrature(op, s));
   STBEM_CUDA(cudaEventRecord(e1, s));
@@ -448,19 +492,11 @@ bem_status stbem::operator_create(bem_context* ctx, const bem_mesh* mesh, const 
     return BEM_ERR_INVALID_ARG;
   }
   STBEM_CUDA(cudaSetDevice(ctx->device));
-  std::unique_ptr<bem_operator> op(new bem_operator());
-  op->ctx = ctx; op->mesh = mesh; op->opts = o;
-  op->mq = o.m_q; op->nq = o.m_q * o.m_q; op->n_theta = o.n_theta;
+  std::unique_ptr<bem_operator> op;
+  bem_status st = op_structure_alloc(ctx, mesh, &o, op);
+  if (st != BEM_OK) { if (op) bem_operator_destroy(op.release()); return st; }
   op->admit = std::move(admit);
-  const int64_t nb = mesh->n_col * mesh->n_col;
-  TRY(dalloc(&op->d_pts, (size_t)mesh->n_surf * op->nq * 4));
-  TRY(dalloc(&op->d_pts_trange, (size_t)mesh->n_surf * 2));
-  TRY(dalloc(&op->d_bw, (size_t)nb));
-  TRY(dalloc(&op->d_bnnz, (size_t)nb));
-  TRY(dalloc(&op->d_boff, (size_t)nb));
-  TRY(dalloc(&op->d_rsoff, (size_t)nb));
-  TRY(dalloc(&op->d_counter, 4));
-  bem_status st = assemble(op.get(), ctx->stream, true);
+  st = assemble(op.get(), ctx->stream, true);
   if (st != BEM_OK) { bem_operator_destroy(op.release()); return st; }
   int64_t nbad = 0;
   double mx = 0.0;

@@ -362,29 +362,23 @@ __device__ void face_bits(const BlockCtx& B, const ColSm& C, const TetSm* T, int
   }
 }
 
-__device__ inline int64_t pop_block(const BlockCtx& B) {
+__device__ inline int64_t pop_block(unsigned long long* counter) {
   __shared__ unsigned long long s_b;
-  if (threadIdx.x == 0) s_b = atomicAdd(B.counter, 1ull);
+  if (threadIdx.x == 0) s_b = atomicAdd(counter, 1ull);
   __syncthreads();
   int64_t b = (int64_t)s_b;
   __syncthreads();
   return b;
 }
 
-// Pass 1: band width and pattern count of every column block.
-__global__ void __launch_bounds__(128) k_pattern_blocks(BlockCtx B) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ ColSm C;
+// Pass 1: band width and pattern count of column block b.
+__device__ __forceinline__ void pattern_block(const BlockCtx& B, int64_t b, unsigned char* smem, ColSm& C, int* s_w,
+                                              unsigned long long* s_n) {
   TetSm* T = reinterpret_cast<TetSm*>(smem);
   FaceGeom* Fs = reinterpret_cast<FaceGeom*>(T + B.max_tet);
   uint32_t* bits = reinterpret_cast<uint32_t*>(Fs + B.max_surf);
   const int words = (B.max_tet + 31) / 32;
-  __shared__ int s_w[4];
-  __shared__ unsigned long long s_n[4];
-  const int64_t nblk = B.n_col * B.n_col;
-  for (;;) {
-    int64_t b = pop_block(B);
-    if (b >= nblk) break;
+  {
     int64_t I = b / B.n_col, J = b % B.n_col;
     load_column(B, J, C, T, Fs);
     const ColGeom GI = B.cols[I];
@@ -431,13 +425,63 @@ __global__ void __launch_bounds__(128) k_pattern_blocks(BlockCtx B) {
   }
 }
 
-// Pass 2: quadrature and assembly of every non-empty block.
-template <bool FP32>
-__global__ void __launch_bounds__(128, 4) k_quad_blocks(BlockCtx B) {
-  typedef typename std::conditional<FP32, float, double>::type R;
+// segment of global work item g: prefix[seg] <= g < prefix[seg + 1]
+__device__ inline int find_seg(const int64_t* prefix, int S, int64_t g) {
+  int lo = 0, hi = S;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= g) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(128) k_pattern_blocks(BlockCtx B) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ColSm C;
-  __shared__ ColR<R> CR;
+  __shared__ int s_w[4];
+  __shared__ unsigned long long s_n[4];
+  const int64_t nblk = B.n_col * B.n_col;
+  for (;;) {
+    int64_t b = pop_block(B.counter);
+    if (b >= nblk) break;
+    pattern_block(B, b, smem, C, s_w, s_n);
+  }
+}
+
+// The same over the blocks of a batch of operators (one work queue; the
+// contexts share the largest column sizes so the shared layout is uniform).
+__global__ void __launch_bounds__(128) k_pattern_batch(const BlockCtx* __restrict__ Bs,
+                                                       const int64_t* __restrict__ prefix, int S,
+                                                       unsigned long long* counter) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ColSm C;
+  __shared__ int s_w[4];
+  __shared__ unsigned long long s_n[4];
+  __shared__ BlockCtx sB;
+  __shared__ int s_seg;
+  int cur = -1;
+  const int64_t total = prefix[S];
+  for (;;) {
+    int64_t g = pop_block(counter);
+    if (g >= total) break;
+    if (threadIdx.x == 0) s_seg = find_seg(prefix, S, g);
+    __syncthreads();
+    const int seg = s_seg;
+    if (seg != cur) {
+      if (threadIdx.x == 0) sB = Bs[seg];
+      cur = seg;
+    }
+    __syncthreads();
+    pattern_block(sB, g - prefix[seg], smem, C, s_w, s_n);
+  }
+}
+
+// Pass 2: quadrature and assembly of a non-empty block.
+template <bool FP32>
+__device__ __forceinline__ void quad_block(const BlockCtx& B, int64_t b, unsigned char* smem, ColSm& C,
+                                           ColR<typename std::conditional<FP32, float, double>::type>& CR) {
+  typedef typename std::conditional<FP32, float, double>::type R;
   TetSm* T = reinterpret_cast<TetSm*>(smem);
   FaceGeom* Fs = reinterpret_cast<FaceGeom*>(T + B.max_tet);
   uint32_t* bits = reinterpret_cast<uint32_t*>(Fs + B.max_surf);
@@ -445,19 +489,15 @@ __global__ void __launch_bounds__(128, 4) k_quad_blocks(BlockCtx B) {
   PointCol* pc = reinterpret_cast<PointCol*>(bits + ((B.max_surf * words + 3) & ~3));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   PointCol* mypc = pc + warp * B.nq;
-  R* Wsc = reinterpret_cast<R*>(reinterpret_cast<double*>(pc + nw * B.nq) + (size_t)warp * B.nq * B.max_surf);
-  uint16_t* mycut = reinterpret_cast<uint16_t*>(reinterpret_cast<double*>(pc + nw * B.nq) +
-                                                (size_t)nw * B.nq * B.max_surf) + (size_t)warp * B.nq * B.max_surf;
-  FaceF* Ff = reinterpret_cast<FaceF*>(reinterpret_cast<uint16_t*>(reinterpret_cast<double*>(pc + nw * B.nq) +
-                                                                   (size_t)nw * B.nq * B.max_surf) +
-                                       ((size_t)nw * B.nq * B.max_surf + 7) / 8 * 8);
+  R* Wsc0 = reinterpret_cast<R*>(pc + nw * B.nq);
+  R* Wsc = Wsc0 + (size_t)warp * B.nq * B.max_surf;
+  uint16_t* cut0 = reinterpret_cast<uint16_t*>(Wsc0 + (size_t)nw * B.nq * B.max_surf);
+  uint16_t* mycut = cut0 + (size_t)warp * B.nq * B.max_surf;
+  FaceF* Ff = reinterpret_cast<FaceF*>(cut0 + ((size_t)nw * B.nq * B.max_surf + 7) / 8 * 8);
   R* U = reinterpret_cast<R*>(B.uscratch) + (size_t)blockIdx.x * B.max_surf * B.max_tet;
-  const int64_t nblk = B.n_col * B.n_col;
-  for (;;) {
-    int64_t b = pop_block(B);
-    if (b >= nblk) break;
+  {
     int W = B.bw[b];
-    if (W == 0) continue;
+    if (W == 0) return;
     int64_t I = b / B.n_col, J = b % B.n_col;
     load_column(B, J, C, T, Fs);
     if (threadIdx.x == 0) make_colr<R>(C.G, CR);
@@ -573,6 +613,52 @@ __global__ void __launch_bounds__(128, 4) k_quad_blocks(BlockCtx B) {
   }
 }
 
+// CTAs of 128 threads resident per SM that the register budget is cut for
+#ifndef STBEM_QUAD_MIN_CTAS
+#define STBEM_QUAD_MIN_CTAS 4
+#endif
+
+template <bool FP32>
+__global__ void __launch_bounds__(128, STBEM_QUAD_MIN_CTAS) k_quad_blocks(BlockCtx B) {
+  typedef typename std::conditional<FP32, float, double>::type R;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ColSm C;
+  __shared__ ColR<R> CR;
+  const int64_t nblk = B.n_col * B.n_col;
+  for (;;) {
+    int64_t b = pop_block(B.counter);
+    if (b >= nblk) break;
+    quad_block<FP32>(B, b, smem, C, CR);
+  }
+}
+
+template <bool FP32>
+__global__ void __launch_bounds__(128, STBEM_QUAD_MIN_CTAS) k_quad_batch(const BlockCtx* __restrict__ Bs,
+                                                       const int64_t* __restrict__ prefix, int S,
+                                                       unsigned long long* counter) {
+  typedef typename std::conditional<FP32, float, double>::type R;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ColSm C;
+  __shared__ ColR<R> CR;
+  __shared__ BlockCtx sB;
+  __shared__ int s_seg;
+  int cur = -1;
+  const int64_t total = prefix[S];
+  for (;;) {
+    int64_t g = pop_block(counter);
+    if (g >= total) break;
+    if (threadIdx.x == 0) s_seg = find_seg(prefix, S, g);
+    __syncthreads();
+    const int seg = s_seg;
+    if (seg != cur) {
+      if (threadIdx.x == 0) sB = Bs[seg];
+      cur = seg;
+    }
+    __syncthreads();
+    quad_block<FP32>(sB, g - prefix[seg], smem, C, CR);
+  }
+}
+
 static size_t block_smem(const bem_operator* op, bool quad) {
   const bem_mesh* m = op->mesh;
   int words = (m->max_col_tets + 31) / 32;
@@ -580,7 +666,7 @@ static size_t block_smem(const bem_operator* op, bool quad) {
   s += sizeof(uint32_t) * ((m->max_col_surf * words + 3) & ~3);
   if (quad) {
     s += sizeof(PointCol) * 4 * op->nq;
-    s += sizeof(double) * 4 * op->nq * m->max_col_surf;
+    s += (op->opts.precision == BEM_PREC_MIXED ? sizeof(float) : sizeof(double)) * 4 * op->nq * m->max_col_surf;
     s += sizeof(uint16_t) * (((size_t)4 * op->nq * m->max_col_surf + 7) / 8 * 8);
     s += sizeof(FaceF) * m->max_col_surf;
   }
@@ -656,6 +742,125 @@ bem_status op_quadrature(bem_operator* op, cudaStream_t s) {
   STBEM_CUDA(cudaGetLastError());
   return BEM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batched passes: one persistent launch over the blocks of several operators.
+// All contexts take the largest column sizes of the batch, so the shared
+// memory layout is the same for every block, and the quadrature scratch
+// (one slab per CTA) is shared.
+// ---------------------------------------------------------------------------
+bem_status op_outer_points_all(const std::vector<bem_operator*>& ops, cudaStream_t s) {
+  for (bem_operator* op : ops) {
+    bem_status st = op_outer_points(op, s);
+    if (st != BEM_OK) return st;
+  }
+  return BEM_OK;
+}
+
+static void batch_dims(const std::vector<bem_operator*>& ops, int& max_tet, int& max_surf) {
+  max_tet = 1;
+  max_surf = 1;
+  for (const bem_operator* op : ops) {
+    max_tet = std::max(max_tet, op->mesh->max_col_tets);
+    max_surf = std::max(max_surf, op->mesh->max_col_surf);
+  }
+}
+
+static size_t batch_smem(int max_tet, int max_surf, int nq, bool quad, bool fp32 = false) {
+  int words = (max_tet + 31) / 32;
+  size_t s = sizeof(TetSm) * max_tet + sizeof(FaceGeom) * max_surf;
+  s += sizeof(uint32_t) * ((max_surf * words + 3) & ~3);
+  if (quad) {
+    s += sizeof(PointCol) * 4 * nq;
+    s += (fp32 ? sizeof(float) : sizeof(double)) * 4 * nq * max_surf;
+    s += sizeof(uint16_t) * (((size_t)4 * nq * max_surf + 7) / 8 * 8);
+    s += sizeof(FaceF) * max_surf;
+  }
+  return s;
+}
+
+static bem_status upload_batch(const std::vector<bem_operator*>& ops, BatchDev& dev, int max_tet, int max_surf,
+                               cudaStream_t s) {
+  const int S = (int)ops.size();
+  std::vector<BlockCtx> ctx(S);
+  std::vector<int64_t> prefix(S + 1, 0);
+  for (int i = 0; i < S; ++i) {
+    ctx[i] = make_ctx(ops[i]);
+    ctx[i].max_tet = max_tet;
+    ctx[i].max_surf = max_surf;
+    ctx[i].uscratch = dev.d_uscratch;
+    ctx[i].counter = dev.d_counter;
+    prefix[i + 1] = prefix[i] + ops[i]->mesh->n_col * ops[i]->mesh->n_col;
+  }
+  STBEM_CUDA(cudaMemcpyAsync(dev.d_ctx, ctx.data(), sizeof(BlockCtx) * S, cudaMemcpyHostToDevice, s));
+  STBEM_CUDA(cudaMemcpyAsync(dev.d_prefix, prefix.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, s));
+  STBEM_CUDA(cudaMemsetAsync(dev.d_counter, 0, sizeof(unsigned long long), s));
+  STBEM_CUDA(cudaStreamSynchronize(s));   // the host arrays above go out of scope
+  return BEM_OK;
+}
+
+bem_status op_pattern_batch(const std::vector<bem_operator*>& ops, BatchDev& dev, cudaStream_t s) {
+  if (ops.empty()) return BEM_OK;
+  int mt, ms;
+  batch_dims(ops, mt, ms);
+  bem_status st = upload_batch(ops, dev, mt, ms, s);
+  if (st != BEM_OK) return st;
+  const size_t smem = batch_smem(mt, ms, ops[0]->nq, false);
+  STBEM_CUDA(cudaFuncSetAttribute(k_pattern_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = persistent_grid((const void*)k_pattern_batch, smem, 128);
+  k_pattern_batch<<<grid, 128, smem, s>>>(static_cast<const BlockCtx*>(dev.d_ctx), dev.d_prefix, (int)ops.size(),
+                                          dev.d_counter);
+  STBEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+static int quad_batch_grid(const std::vector<bem_operator*>& ops, size_t& smem) {
+  int mt, ms;
+  batch_dims(ops, mt, ms);
+  smem = batch_smem(mt, ms, ops[0]->nq, true, ops[0]->opts.precision == BEM_PREC_MIXED);
+  if (ops[0]->opts.precision == BEM_PREC_MIXED) {
+    cudaFuncSetAttribute(k_quad_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return persistent_grid((const void*)k_quad_batch<true>, smem, 128);
+  }
+  cudaFuncSetAttribute(k_quad_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return persistent_grid((const void*)k_quad_batch<false>, smem, 128);
+}
+
+int64_t quad_batch_scratch(const std::vector<bem_operator*>& ops) {
+  if (ops.empty()) return 0;
+  int mt, ms;
+  batch_dims(ops, mt, ms);
+  size_t smem = 0;
+  return (int64_t)quad_batch_grid(ops, smem) * mt * ms;
+}
+
+bem_status op_quadrature_batch(const std::vector<bem_operator*>& ops, BatchDev& dev, cudaStream_t s) {
+  if (ops.empty()) return BEM_OK;
+  for (const bem_operator* op : ops)
+    if (op->opts.precision != ops[0]->opts.precision || op->nq != ops[0]->nq || op->n_theta != ops[0]->n_theta) {
+      set_error("a batch takes one precision, m_Q and n_theta");
+      return BEM_ERR_INVALID_ARG;
+    }
+  if (dev.uscratch_len < quad_batch_scratch(ops)) {
+    set_error("batch quadrature scratch too small");
+    return BEM_ERR_INTERNAL;
+  }
+  int mt, ms;
+  batch_dims(ops, mt, ms);
+  bem_status st = upload_batch(ops, dev, mt, ms, s);
+  if (st != BEM_OK) return st;
+  size_t smem = 0;
+  const int grid = quad_batch_grid(ops, smem);
+  const BlockCtx* d = static_cast<const BlockCtx*>(dev.d_ctx);
+  if (ops[0]->opts.precision == BEM_PREC_MIXED)
+    k_quad_batch<true><<<grid, 128, smem, s>>>(d, dev.d_prefix, (int)ops.size(), dev.d_counter);
+  else
+    k_quad_batch<false><<<grid, 128, smem, s>>>(d, dev.d_prefix, (int)ops.size(), dev.d_counter);
+  STBEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+size_t block_ctx_size() { return sizeof(BlockCtx); }
 
 // ---------------------------------------------------------------------------
 // Value scan: non-finite count and largest magnitude
@@ -745,7 +950,7 @@ __global__ void __launch_bounds__(128) k_pattern_rows(BlockCtx B, int64_t* rowco
   const int words = (B.max_tet + 31) / 32;
   const int64_t nblk = I_only >= 0 ? B.n_col : B.n_col * B.n_col;
   for (;;) {
-    int64_t b = pop_block(B);
+    int64_t b = pop_block(B.counter);
     if (b >= nblk) break;
     if (I_only >= 0) b += I_only * B.n_col;
     if (B.bw[b] == 0) continue;

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <functional>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -84,6 +85,7 @@ struct bem_operator {
   double* d_val = nullptr;       // values, per block column-major [W][R_I]
   float* d_val32 = nullptr;
   int64_t nnz = 0, nstored = 0, nblocks = 0, nrows_stored = 0;
+  int max_bw = 0;                // widest band of any block
   double assemble_ms = 0.0;
   double phase_ms[4] = {0, 0, 0, 0};
   unsigned long long* d_counter = nullptr;  // work counter of the persistent kernels
@@ -107,9 +109,67 @@ bem_status mesh_device_geometry(bem_mesh* m, const double* d_sv_xyz, const int32
 bem_status op_outer_points(bem_operator* op, cudaStream_t s);
 bem_status op_pattern(bem_operator* op, cudaStream_t s);
 bem_status op_quadrature(bem_operator* op, cudaStream_t s);
+// Layout of the vectors of a batched GMRES: K vectors of length N ([K][N]);
+// entries [seg_off[s], seg_off[s+1]) of a vector belong to segment s (one
+// operator of a block-diagonal batch). Each (vector, segment) is a column
+// with its own Krylov process.
+struct SegLayout {
+  int64_t N = 0;
+  int K = 1, S = 1;
+  std::vector<int64_t> seg_off;   // [S+1]
+};
+// y = A x for all K vectors (device arrays in the [K][N] layout), enqueued on s
+using MatvecFn = std::function<bem_status(const double* x, double* y, cudaStream_t s)>;
+bem_status gmres_device(const SegLayout& L, const MatvecFn& mv, const double* d_b, double* d_x, double tol, int m,
+                        int maxit, std::vector<int>& iters, std::vector<double>& relres, std::vector<int>& conv,
+                        cudaStream_t s);
+// block-diagonal product over the operators of a batch ([K][N] vectors,
+// operator i owning entries [off_i, off_i + n_tet_i) of every vector)
+struct BatchMatvec {
+  std::vector<bem_operator*> ops;
+  void* d_segs = nullptr;
+  int32_t* d_cseg = nullptr;
+  int32_t* d_ccol = nullptr;
+  int64_t n_cta = 0, N = 0;
+  int rows_pad = 32, groups = 1;
+  bool fp64_values = false;
+  float* d_xf = nullptr;
+  int64_t xf_len = 0;
+  bem_status init(const std::vector<bem_operator*>& o, cudaStream_t s);
+  bem_status apply(const double* x, double* y, int K, int arith, cudaStream_t s);
+  ~BatchMatvec();
+};
+// per-column 2-norms of a [K][N] vector (host result)
+bem_status seg_norms(const SegLayout& L, const double* v, std::vector<double>& out, cudaStream_t s);
+// refined solve over a layout: FP64 GMRES with mv_hi, or inner GMRES with
+// mv_lo inside FP64 refinement (o->inner_dtype != FP64); info per column
+bem_status gmres_solve_layout(const SegLayout& L, const MatvecFn& mv_hi, const MatvecFn& mv_lo, const double* d_b,
+                              double* d_x, const bem_solve_opts* o, bem_solve_info* info, cudaStream_t s);
 // operator creation with an admission hook (see bem_operator::admit)
 bem_status operator_create(bem_context* ctx, const bem_mesh* mesh, const bem_op_opts* opts,
                            std::function<bem_status(const bem_operator*)> admit, bem_operator** out);
+// operator object with its structure arrays allocated (nothing assembled yet)
+bem_status op_structure_alloc(bem_context* ctx, const bem_mesh* mesh, const bem_op_opts* opts,
+                              std::unique_ptr<bem_operator>& op);
+// block offsets from the per-block band widths and counts (host arrays);
+// first: set the storage sizes, call the admission hook, allocate the values
+// (and the quadrature scratch when own_scratch)
+bem_status op_layout(bem_operator* op, const int32_t* bw, const int64_t* bnnz, bool first, bool own_scratch,
+                     cudaStream_t s);
+// batched pattern and quadrature passes over several operators (one
+// persistent launch each); the operators share `uscratch` for the quadrature
+struct BatchDev {
+  void* d_ctx = nullptr;                 // BlockCtx[S]
+  int64_t* d_prefix = nullptr;           // [S+1] block prefix
+  unsigned long long* d_counter = nullptr;
+  double* d_uscratch = nullptr;
+  int64_t uscratch_len = 0;
+};
+bem_status op_outer_points_all(const std::vector<bem_operator*>& ops, cudaStream_t s);
+bem_status op_pattern_batch(const std::vector<bem_operator*>& ops, BatchDev& dev, cudaStream_t s);
+bem_status op_quadrature_batch(const std::vector<bem_operator*>& ops, BatchDev& dev, cudaStream_t s);
+int64_t quad_batch_scratch(const std::vector<bem_operator*>& ops);
+size_t block_ctx_size();
 // bytes held by an operator's value arrays, row starts and quadrature scratch
 int64_t operator_value_bytes(const bem_operator* op);
 // arithmetic of a product (values equal to BEM_DTYPE_*)

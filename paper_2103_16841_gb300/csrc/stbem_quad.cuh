@@ -209,8 +209,9 @@ STBEM_HD inline R edge_dE(R wa, R dw, R p_s, R d) {
 // free of cancellation, and analytic up to the branch points w = +-iA. In
 // FP32 the closed form above loses the relative accuracy of such an edge:
 // its asinh and atan terms are O(1) with a difference of O(dw / A). Returns
-// false when the branch points are too close for n_max nodes (Bernstein
-// parameter below 3); the caller then takes the closed form.
+// false when the branch points are close (Bernstein parameter below 4, or
+// more than six nodes needed): there the edge is not far from the apex, the
+// closed form keeps its accuracy, and the caller takes it.
 template <typename R>
 STBEM_HD inline bool edge_gauss(R wa, R dw, R p_s, R d, const ArcRule& rule, R& out) {
   R A2 = p_s * p_s + d * d;
@@ -219,9 +220,10 @@ STBEM_HD inline bool edge_gauss(R wa, R dw, R p_s, R d, const ArcRule& rule, R& 
   R a = -m / hl, b = sqrt(A2) / fabs(hl);
   R s = R(0.5) * (sqrt((a - R(1)) * (a - R(1)) + b * b) + sqrt((a + R(1)) * (a + R(1)) + b * b));
   R rho = s + sqrt(fmax(s * s - R(1), R(0)));
-  if (!(rho >= R(3))) return false;
+  if (!(rho >= R(4))) return false;
   int n = (int)ceil(log(R(1.0 / rule.tol)) / (R(2) * log(rho))) + 1;
-  n = n < 2 ? 2 : (n > rule.nmax ? rule.nmax : n);
+  if (n > 6) return false;   // the closed form costs about as much as six nodes
+  n = n < 2 ? 2 : n;
   const double* X = gl_x() + n * (n - 1) / 2;
   const double* Wt = gl_w() + n * (n - 1) / 2;
   R ad = fabs(d), acc = R(0);
