@@ -155,6 +155,21 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def aggregate(ms, pairs, device):
+    """Whole-job numbers of a weak-scaling step: the slowest rank's time and
+    the pairs of all ranks (each rank assembles its own mesh; no collective
+    touches the data path)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(ms), float(pairs)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    n = torch.tensor([float(pairs)], dtype=torch.float64, device=device)
+    tdist.all_reduce(n)
+    return float(t.item()), float(n.item())
+
+
 def run_ours(args):
     import torch
     import paper_2103_16841_gb300 as stb
@@ -204,17 +219,7 @@ def run_ours(args):
         ev1.synchronize()
         barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
-    t_local = ms
-    if dist:
-        import torch.distributed as tdist
-        t = torch.tensor([ms], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
-        n_all = torch.tensor([float(nnz)], device="cuda")
-        tdist.all_reduce(n_all)
-        total_pairs = float(n_all.item())
-    else:
-        total_pairs = float(nnz)
+    ms, total_pairs = aggregate(ms, nnz, "cuda")
     value = total_pairs / (ms / 1e3)
     quad_ms = float(np.mean([p["quadrature_ms"] for p in phases]))
 
@@ -237,11 +242,7 @@ def run_ours(args):
         op2.close()
         mesh2.close()
     t_e2e = max(e2e_times) if e2e_times else float("nan")
-    if dist:
-        import torch.distributed as tdist
-        t = torch.tensor([t_e2e], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e, _ = aggregate(t_e2e, 0, "cuda")
     d2h = m.n_tet * 8 + m.n_tet * 8  # rhs vector and density back to the host
 
     multi = multi_rhs_leg(op, m, args) if args.multi_rhs > 0 else None

@@ -216,7 +216,6 @@ struct SpmmArgs {
   const uint32_t* X;    // packed x
   float* Y;             // [n_tet][8 NT8]
   int strips;           // ceil(max rows per column / 16)
-  int wmax;             // widest band (rows of a warp's band tile)
 };
 
 template <int NT8>
@@ -238,104 +237,77 @@ __device__ __forceinline__ void load_b(const uint32_t* p, uint32_t (&b)[NT8]) {
 
 // One CTA per test column I: warp (strip, ws) owns rows 16 strip .. +15 and
 // the trial columns J = ws, ws + WS, ...; the WS partial tiles of a strip are
-// summed in a fixed order at the end. Per block, the warp copies the band
-// values of its 16 rows (W x 16, coalesced: 16 lanes per band column) into
-// its shared tile, then builds the MMA fragments from the tile; the block
-// metadata of the next J is fetched while the current one is computed.
+// summed in a fixed order at the end.
 template <bool BF16, int NT8, int WS>
 __global__ void __launch_bounds__(512) k_spmm(SpmmArgs a) {
-  typedef typename std::conditional<BF16, uint16_t, float>::type VT;
-  extern __shared__ __align__(16) unsigned char sm_raw[];
+  extern __shared__ float sred[];
   constexpr int NRp = NT8 * 8;
   const int64_t I = blockIdx.x;
   const int t0 = a.ctb[I], nt = a.ctb[I + 1] - t0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = blockDim.x >> 5;
   const int strip = warp % a.strips, ws = warp / a.strips;
   const int g = lane >> 2, t = lane & 3;
   const int r0 = strip * 16 + g, r1 = r0 + 8;
   const bool v0 = r0 < nt, v1 = r1 < nt;
   const bool any_rows = strip * 16 < nt;
-  VT* tile = reinterpret_cast<VT*>(sm_raw) + (size_t)warp * a.wmax * 16;
-  float* sred = reinterpret_cast<float*>(sm_raw + (((size_t)nwarps * a.wmax * 16 * sizeof(VT) + 15) & ~(size_t)15));
-  const VT* val = static_cast<const VT*>(a.val);
-  const int lr = lane & 15, lh = lane >> 4;            // tile loader: row, column parity
-  const bool lrow = strip * 16 + lr < nt;
   float acc[NT8][4];
 #pragma unroll
   for (int q = 0; q < NT8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
   if (any_rows) {
-    int64_t J = ws;
-    int W_n = 0, je_n = 0;
-    int64_t vo_n = 0, ro_n = 0;
-    if (J < a.n_col) {
+    for (int64_t J = ws; J < a.n_col; J += WS) {
       const int64_t b = I * a.n_col + J;
-      W_n = a.bw[b]; vo_n = a.boff[b]; ro_n = a.rsoff[b]; je_n = a.ctb[J + 1];
-    }
-    for (; J < a.n_col; J += WS) {
-      const int W = W_n, je = je_n;
-      const int64_t vo = vo_n, ro = ro_n;
-      const int64_t Jn = J + WS;
-      if (Jn < a.n_col) {
-        const int64_t b = I * a.n_col + Jn;
-        W_n = a.bw[b]; vo_n = a.boff[b]; ro_n = a.rsoff[b]; je_n = a.ctb[Jn + 1];
-      }
+      const int W = a.bw[b];
       if (W == 0) continue;
-      // row starts of the strip (lanes 0..15) and the band tile
-      const int rsv = (lane < 16 && lrow) ? __ldg(a.rs + ro + strip * 16 + lane) : INT_MAX;
-      {
-        const VT* src = val + vo + strip * 16 + lr;
-#pragma unroll 4
-        for (int w = lh; w < W; w += 2) tile[w * 16 + lr] = lrow ? __ldg(src + (int64_t)w * nt) : VT(0);
-      }
-      const int s0 = __shfl_sync(0xffffffffu, rsv, g);
-      const int s1 = __shfl_sync(0xffffffffu, rsv, g + 8);
-      int smin = rsv, smax = rsv == INT_MAX ? INT_MIN : rsv;
+      const int64_t vo = a.boff[b], ro = a.rsoff[b];
+      const int je = a.ctb[J + 1];
+      const int s0 = v0 ? a.rs[ro + r0] : INT_MAX;
+      const int s1 = v1 ? a.rs[ro + r1] : INT_MAX;
+      int smin = min(s0, s1);
+      int smax = max(v0 ? s0 : INT_MIN, v1 ? s1 : INT_MIN);
 #pragma unroll
-      for (int o = 8; o > 0; o >>= 1) {
+      for (int o = 16; o >= 4; o >>= 1) {
         smin = min(smin, __shfl_xor_sync(0xffffffffu, smin, o));
         smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, o));
       }
-      smin = __shfl_sync(0xffffffffu, smin, 0);
-      smax = __shfl_sync(0xffffffffu, smax, 0);
-      __syncwarp();
       int c0 = smin;
       if (BF16) c0 &= ~1;
       const int K = smax + W - c0;
-      // tile element of row rr (start s) at trial column c, 0 outside the band
-      auto el = [&](bool v, int rr, int s, int c) -> uint32_t {
-        const int w = c - s;
-        if (!(v && w >= 0 && w < W && c < je)) return 0u;
-        if constexpr (BF16) return (uint32_t)tile[w * 16 + rr];
-        else return to_tf32(tile[w * 16 + rr]);
-      };
-      if constexpr (!BF16) {
+      if (!BF16) {
+        const float* val = static_cast<const float*>(a.val) + vo;
+        auto ld = [&](bool v, int r, int s, int c) -> uint32_t {
+          const int w = c - s;
+          return (v && w >= 0 && w < W && c < je) ? to_tf32(__ldg(val + (int64_t)w * nt + r)) : 0u;
+        };
         for (int k0 = 0; k0 < K; k0 += 8) {
           const int ca = c0 + k0 + t, cb = ca + 4;
+          const uint32_t A0 = ld(v0, r0, s0, ca), A1 = ld(v1, r1, s1, ca);
+          const uint32_t A2 = ld(v0, r0, s0, cb), A3 = ld(v1, r1, s1, cb);
           uint32_t B0[NT8], B1[NT8];
           load_b<NT8>(a.X + (int64_t)min(ca, je - 1) * NRp + g * NT8, B0);
           load_b<NT8>(a.X + (int64_t)min(cb, je - 1) * NRp + g * NT8, B1);
-          const uint32_t A0 = el(v0, g, s0, ca), A1 = el(v1, g + 8, s1, ca);
-          const uint32_t A2 = el(v0, g, s0, cb), A3 = el(v1, g + 8, s1, cb);
 #pragma unroll
           for (int q = 0; q < NT8; ++q) mma_tf32(acc[q], A0, A1, A2, A3, B0[q], B1[q]);
         }
       } else {
+        const uint16_t* val = static_cast<const uint16_t*>(a.val) + vo;
+        auto ld = [&](bool v, int r, int s, int c) -> uint32_t {
+          const int w = c - s;
+          return (v && w >= 0 && w < W && c < je) ? (uint32_t)__ldg(val + (int64_t)w * nt + r) : 0u;
+        };
         const int plast = (je - 1) >> 1;
         for (int k0 = 0; k0 < K; k0 += 16) {
           const int pa = c0 + k0 + 2 * t, pb = pa + 8;
+          const uint32_t A0 = ld(v0, r0, s0, pa) | (ld(v0, r0, s0, pa + 1) << 16);
+          const uint32_t A1 = ld(v1, r1, s1, pa) | (ld(v1, r1, s1, pa + 1) << 16);
+          const uint32_t A2 = ld(v0, r0, s0, pb) | (ld(v0, r0, s0, pb + 1) << 16);
+          const uint32_t A3 = ld(v1, r1, s1, pb) | (ld(v1, r1, s1, pb + 1) << 16);
           uint32_t B0[NT8], B1[NT8];
           load_b<NT8>(a.X + (int64_t)min(pa >> 1, plast) * NRp + g * NT8, B0);
           load_b<NT8>(a.X + (int64_t)min(pb >> 1, plast) * NRp + g * NT8, B1);
-          const uint32_t A0 = el(v0, g, s0, pa) | (el(v0, g, s0, pa + 1) << 16);
-          const uint32_t A1 = el(v1, g + 8, s1, pa) | (el(v1, g + 8, s1, pa + 1) << 16);
-          const uint32_t A2 = el(v0, g, s0, pb) | (el(v0, g, s0, pb + 1) << 16);
-          const uint32_t A3 = el(v1, g + 8, s1, pb) | (el(v1, g + 8, s1, pb + 1) << 16);
 #pragma unroll
           for (int q = 0; q < NT8; ++q) mma_bf16(acc[q], A0, A1, A2, A3, B0[q], B1[q]);
         }
       }
-      __syncwarp();
     }
   }
   if constexpr (WS > 1) {
@@ -408,15 +380,10 @@ bem_status ensure_val16(const bem_operator* op, cudaStream_t s) {
 std::mutex g_tune_mu;
 std::map<std::tuple<int64_t, int, int, int, int>, int> g_tuned;
 
-size_t spmm_smem(int strips, int ws, int nt8, int wmax, bool bf16) {
-  const size_t tiles = ((size_t)strips * ws * wmax * 16 * (bf16 ? 2 : 4) + 15) & ~(size_t)15;
-  return tiles + (ws > 1 ? sizeof(float) * (size_t)(ws - 1) * strips * nt8 * 4 * 32 : 0);
-}
-
 template <bool BF16, int NT8, int WS>
 bem_status launch_spmm_ws(const SpmmArgs& a, cudaStream_t s) {
   const int threads = a.strips * WS * 32;
-  const size_t smem = spmm_smem(a.strips, WS, NT8, a.wmax, BF16);
+  const size_t smem = WS > 1 ? sizeof(float) * (size_t)(WS - 1) * a.strips * NT8 * 4 * 32 : 0;
   if (smem > 48 * 1024)
     STBEM_CUDA(cudaFuncSetAttribute(k_spmm<BF16, NT8, WS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_spmm<BF16, NT8, WS><<<(unsigned)a.n_col, threads, smem, s>>>(a);
@@ -434,14 +401,14 @@ bem_status launch_spmm(const SpmmArgs& a, int ws, cudaStream_t s) {
   }
 }
 
-bool ws_ok(int strips, int nt8, int ws, int wmax, bool bf16) {
-  return strips * ws <= 16 && spmm_smem(strips, ws, nt8, wmax, bf16) <= 160 * 1024;
+bool ws_ok(int strips, int nt8, int ws) {
+  return strips * ws <= 16 && (ws == 1 || (size_t)(ws - 1) * strips * nt8 * 4 * 32 * 4 <= 100 * 1024);
 }
 
 template <bool BF16, int NT8>
 bem_status run_spmm(const bem_operator* op, const SpmmArgs& a, cudaStream_t s) {
-  const auto key = std::make_tuple(op->mesh->n_col, op->mesh->max_col_tets, NT8, (int)BF16 + 2 * a.wmax,
-                                   op->ctx->device);
+  const auto key = std::make_tuple(op->mesh->n_col, op->mesh->max_col_tets, NT8, (int)BF16, op->ctx->device);
+  // candidates differ in summation order: the choice is kept per shape for the process
   int ws = 0;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -457,7 +424,7 @@ bem_status run_spmm(const bem_operator* op, const SpmmArgs& a, cudaStream_t s) {
   int best_ws = 1;
   bem_status st = BEM_OK;
   for (int c : {1, 2, 4, 8}) {
-    if (!ws_ok(a.strips, NT8, c, a.wmax, BF16)) continue;
+    if (!ws_ok(a.strips, NT8, c)) continue;
     if ((st = launch_spmm<BF16, NT8>(a, c, s)) != BEM_OK) break;
     cudaEventRecord(e0, s);
     if ((st = launch_spmm<BF16, NT8>(a, c, s)) != BEM_OK) break;
@@ -471,7 +438,7 @@ bem_status run_spmm(const bem_operator* op, const SpmmArgs& a, cudaStream_t s) {
   cudaEventDestroy(e1);
   if (st != BEM_OK) return st;
   if (best >= 1e30f) {
-    set_error("tensor-core product: no launch shape fits the band width of this operator");
+    set_error("tensor-core product: no launch shape fits this operator");
     return BEM_ERR_UNSUPPORTED;
   }
   {
@@ -497,8 +464,8 @@ bem_status spmm_nt8(const bem_operator* op, const SpmmArgs& a, int nt8, cudaStre
 int spmm_tuned_ws(const bem_operator* op, int nrhs, int arith) {
   int nt8 = nrhs <= 8 ? 1 : nrhs <= 16 ? 2 : nrhs <= 32 ? 4 : 8;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  auto it = g_tuned.find(std::make_tuple(op->mesh->n_col, op->mesh->max_col_tets, nt8,
-                                         (int)(arith == MV_BF16) + 2 * std::max(op->max_bw, 1), op->ctx->device));
+  auto it = g_tuned.find(std::make_tuple(op->mesh->n_col, op->mesh->max_col_tets, nt8, (int)(arith == MV_BF16),
+                                         op->ctx->device));
   return it == g_tuned.end() ? 0 : it->second;
 }
 
@@ -541,7 +508,6 @@ bem_status op_matvec(const bem_operator* op, const double* x, double* y, int nrh
       a.X = Xp;
       a.Y = Yp;
       a.strips = (m->max_col_tets + 15) / 16;
-      a.wmax = std::max(op->max_bw, 1);
       st = bf16 ? spmm_nt8<true>(op, a, nt8, s) : spmm_nt8<false>(op, a, nt8, s);
       if (st != BEM_OK) return st;
       k_unpack_y<<<grid_for(n * nr), 256, 0, s>>>(Yp, NRp, n, nr, y + (int64_t)r0 * n);
