@@ -130,6 +130,9 @@ typedef struct {
                         complex pole to reach 1e-15 (FP64) or 1e-7 (MIXED) relative accuracy. */
   int32_t store_fp32;/* FP64 operators: 1 also keeps an FP32 copy of the values for low-precision
                         matvecs. MIXED operators always store FP32 values only (their accuracy). */
+  int32_t matrix_free;/* 1: no values are stored; every product re-runs the quadrature with the
+                        entries summed against x on the fly (the dot product fused into the
+                        quadrature pass); export_dense / entries are then unsupported. */
 } bem_op_opts;
 
 /* Assembles the sparse Galerkin matrix on the device.

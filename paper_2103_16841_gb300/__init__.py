@@ -98,9 +98,9 @@ class Operator:
     """bem_operator: the assembled energetic single-layer Galerkin matrix."""
 
     def __init__(self, ctx: Context, mesh: Mesh, precision: str = "fp64", m_q: int = 3, n_theta: int = 0,
-                 store_fp32: bool = True):
+                 store_fp32: bool = True, matrix_free: bool = False):
         self.ctx, self.mesh = ctx, mesh
-        o = _lib.OpOpts(_lib.PREC[precision], int(m_q), int(n_theta), int(bool(store_fp32)))
+        o = _lib.OpOpts(_lib.PREC[precision], int(m_q), int(n_theta), int(bool(store_fp32)), int(bool(matrix_free)))
         h = ctypes.c_void_p()
         _lib.check(ctx._L.bem_operator_create(ctx.h, mesh.h, ctypes.byref(o), ctypes.byref(h)))
         self.h = h
@@ -237,7 +237,7 @@ class Batch:
     def __init__(self, ctx: Context, meshes, precision="mixed", m_q=3, n_theta=0, store_fp32=True):
         self.ctx = ctx
         self.meshes = list(meshes)          # the meshes must outlive the batch
-        o = _lib.OpOpts(_lib.PREC[precision], int(m_q), int(n_theta), int(bool(store_fp32)))
+        o = _lib.OpOpts(_lib.PREC[precision], int(m_q), int(n_theta), int(bool(store_fp32)), 0)
         arr = (ctypes.c_void_p * len(self.meshes))(*[mm.h.value for mm in self.meshes])
         h = ctypes.c_void_p()
         _lib.check(ctx._L.bem_batch_create(ctx.h, len(self.meshes), arr, ctypes.byref(o), ctypes.byref(h)))

@@ -43,7 +43,7 @@ class BemError(RuntimeError):
 
 class OpOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("m_q", ctypes.c_int32), ("n_theta", ctypes.c_int32),
-                ("store_fp32", ctypes.c_int32)]
+                ("store_fp32", ctypes.c_int32), ("matrix_free", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):

@@ -376,13 +376,16 @@ bem_status stbem::op_layout(bem_operator* op, const int32_t* bw, const int64_t* 
     } else {
       op->tmp_len = 0;
     }
+    if (op->opts.matrix_free) op->nstored = 0;
     if (op->admit) TRY(op->admit(op));
-    // mixed-precision values carry FP32 accuracy: FP32 storage only
-    if (op->opts.precision == BEM_PREC_FP64) TRY(dalloc(&op->d_val, (size_t)vo));
-    if (op->opts.store_fp32 || op->opts.precision == BEM_PREC_MIXED) TRY(dalloc(&op->d_val32, (size_t)vo));
-    TRY(dalloc(&op->d_rs, (size_t)ro));
+    if (!op->opts.matrix_free) {
+      // mixed-precision values carry FP32 accuracy: FP32 storage only
+      if (op->opts.precision == BEM_PREC_FP64) TRY(dalloc(&op->d_val, (size_t)vo));
+      if (op->opts.store_fp32 || op->opts.precision == BEM_PREC_MIXED) TRY(dalloc(&op->d_val32, (size_t)vo));
+      TRY(dalloc(&op->d_rs, (size_t)ro));
+    }
     if (own_scratch) TRY(dalloc(&op->d_tmp, (size_t)op->tmp_len));
-  } else if (vo != op->nstored || nnz != op->nnz) {
+  } else if ((!op->opts.matrix_free && vo != op->nstored) || nnz != op->nnz) {
     set_error("reassembly changed the sparsity structure");
     return BEM_ERR_INTERNAL;
   }
@@ -443,7 +446,7 @@ bem_status assemble(bem_operator* op, cudaStream_t s, bool first) {
   STBEM_CUDA(cudaStreamSynchronize(s));
   TRY(op_layout(op, bw.data(), bnnz.data(), first, true, s));
   STBEM_CUDA(cudaEventRecord(ec, s));
-  TRY(op_quadrature(op, s));
+  if (!op->opts.matrix_free) TRY(op_quadrature(op, s));
   STBEM_CUDA(cudaEventRecord(e1, s));
   STBEM_CUDA(cudaEventSynchronize(e1));
   float ms = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
@@ -500,7 +503,7 @@ bem_status stbem::operator_create(bem_context* ctx, const bem_mesh* mesh, const 
   if (st != BEM_OK) { bem_operator_destroy(op.release()); return st; }
   int64_t nbad = 0;
   double mx = 0.0;
-  st = op_value_scan(op.get(), &nbad, &mx, ctx->stream);
+  if (!op->opts.matrix_free) st = op_value_scan(op.get(), &nbad, &mx, ctx->stream);
   if (st == BEM_OK && nbad > 0) {
     set_error(std::to_string(nbad) + " assembled values are not finite");
     st = BEM_ERR_INTERNAL;
@@ -514,6 +517,10 @@ bem_status stbem::operator_create(bem_context* ctx, const bem_mesh* mesh, const 
 extern "C" {
 
 bem_status bem_operator_check(const bem_operator* op, int64_t* n_nonfinite, double* max_abs) {
+  if (op && op->opts.matrix_free) {
+    set_error("matrix-free operator: no stored values");
+    return BEM_ERR_UNSUPPORTED;
+  }
   if (!op) { set_error("null operator"); return BEM_ERR_INVALID_ARG; }
   int64_t nb = 0;
   double mx = 0.0;
@@ -633,6 +640,10 @@ bem_status bem_operator_pattern_rows(const bem_operator* op, int64_t n, const in
 }
 
 bem_status bem_operator_export_dense(const bem_operator* op, double* A) {
+  if (op && op->opts.matrix_free) {
+    set_error("matrix-free operator: no stored values");
+    return BEM_ERR_UNSUPPORTED;
+  }
   if (!op || !A) { set_error("invalid argument"); return BEM_ERR_INVALID_ARG; }
   const bem_mesh* m = op->mesh;
   const int64_t n = m->n_tet, nb = m->n_col * m->n_col;
@@ -674,6 +685,10 @@ bem_status bem_operator_export_dense(const bem_operator* op, double* A) {
 }
 
 bem_status bem_operator_entries(const bem_operator* op, int64_t n, const int32_t* ij, double* out) {
+  if (op && op->opts.matrix_free) {
+    set_error("matrix-free operator: no stored values");
+    return BEM_ERR_UNSUPPORTED;
+  }
   if (!op || (n > 0 && (!ij || !out)) || n < 0) { set_error("invalid argument"); return BEM_ERR_INVALID_ARG; }
   if (n == 0) return BEM_OK;
   const bem_mesh* m = op->mesh;

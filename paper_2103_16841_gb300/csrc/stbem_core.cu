@@ -299,6 +299,12 @@ struct BlockCtx {
   double* uscratch;     // [gridDim][max_surf][max_tet]
   int max_surf, max_tet;
   unsigned long long* counter;
+  // matrix-free product: when mf_y is set the entries are not stored but
+  // y[k][i] += A_ij x[k][j] is accumulated (x, y: [mf_nrhs][mf_ld], internal order)
+  const double* mf_x;
+  double* mf_y;
+  int mf_nrhs;
+  int64_t mf_ld;
 };
 
 // cooperative load of column J into shared memory
@@ -598,9 +604,22 @@ __device__ __forceinline__ void quad_block(const BlockCtx& B, int64_t b, unsigne
         if (m) first = 32 * w + __ffs(m) - 1;
       }
       if (first < 0) first = 0;
-      B.rs[roff + r] = C.tet0 + first;
       const R* Ulo = U + (size_t)lo * B.max_tet;
       const R* Uhi = U + (size_t)hi * B.max_tet;
+      if (B.mf_y) {
+        // fused product: the row's band times x, one atomic add per right-hand side
+        for (int k = 0; k < B.mf_nrhs; ++k) {
+          const double* xk = B.mf_x + (int64_t)k * B.mf_ld + C.tet0;
+          double sacc = 0.0;
+          for (int w = 0; w < W; ++w) {
+            const int j = first + w;
+            if (j < ntJ) sacc += (double)(scale * (Ulo[j] - Uhi[j])) * xk[j];
+          }
+          atomicAdd(B.mf_y + (int64_t)k * B.mf_ld + t0 + r, sacc);
+        }
+        continue;
+      }
+      B.rs[roff + r] = C.tet0 + first;
       for (int w = 0; w < W; ++w) {
         int j = first + w;
         R v = R(0);
@@ -698,6 +717,7 @@ static BlockCtx make_ctx(bem_operator* op) {
   B.val = op->d_val; B.val32 = op->d_val32; B.uscratch = op->d_tmp;
   B.max_surf = m->max_col_surf; B.max_tet = m->max_col_tets;
   B.counter = nullptr;
+  B.mf_x = nullptr; B.mf_y = nullptr; B.mf_nrhs = 0; B.mf_ld = m->n_tet;
   return B;
 }
 
@@ -733,6 +753,29 @@ bem_status op_quadrature(bem_operator* op, cudaStream_t s) {
   BlockCtx B = make_ctx(op);
   bem_status st = get_counter(op, &B.counter, s);
   if (st != BEM_OK) return st;
+  size_t smem = block_smem(op, true);
+  int grid = quad_grid(op);
+  if ((int64_t)grid * op->mesh->max_col_surf * op->mesh->max_col_tets > op->tmp_len) {
+    set_error("quadrature scratch too small");
+    return BEM_ERR_INTERNAL;
+  }
+  if (op->opts.precision == BEM_PREC_MIXED) k_quad_blocks<true><<<grid, 128, smem, s>>>(B);
+  else k_quad_blocks<false><<<grid, 128, smem, s>>>(B);
+  STBEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+// Matrix-free product y = A x (internal order, [nrhs][n_tet]): the quadrature
+// pass with the entries summed against x instead of stored.
+bem_status op_matvec_free(const bem_operator* op, const double* x, double* y, int nrhs, cudaStream_t s) {
+  BlockCtx B = make_ctx(const_cast<bem_operator*>(op));
+  bem_status st = get_counter(op, &B.counter, s);
+  if (st != BEM_OK) return st;
+  B.mf_x = x;
+  B.mf_y = y;
+  B.mf_nrhs = nrhs;
+  B.mf_ld = op->mesh->n_tet;
+  STBEM_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * op->mesh->n_tet * nrhs, s));
   size_t smem = block_smem(op, true);
   int grid = quad_grid(op);
   if ((int64_t)grid * op->mesh->max_col_surf * op->mesh->max_col_tets > op->tmp_len) {

@@ -70,13 +70,27 @@ __device__ __forceinline__ void matvec_col(int64_t n_col, const int32_t* __restr
         if (W == 0) continue;
         const int start = rs[ro + r];
         const V* v = val + vo + r;
-#pragma unroll 4
-        for (int w = 0; w < W; ++w) {
-          const int j = min(start + w, jl);
-          const Acc a = (Acc)v[(int64_t)w * nt];
+        // the band values of a chunk are loaded together (more bytes in flight
+        // per warp), then summed in order
+        constexpr int CW = NR == 1 ? 16 : 8;
+        for (int w0 = 0; w0 < W; w0 += CW) {
+          Acc av[CW];
+          int jv[CW];
 #pragma unroll
-          for (int k = 0; k < NR; ++k)
-            if (k < nr) acc[k] += a * (Acc)x[(int64_t)(rh0 + k) * ld + j];
+          for (int u = 0; u < CW; ++u) {
+            const int w = w0 + u;
+            jv[u] = min(start + w, jl);
+            av[u] = w < W ? (Acc)v[(int64_t)w * nt] : Acc(0);
+          }
+#pragma unroll
+          for (int k = 0; k < NR; ++k) {
+            if (k < nr) {
+              const XT* xr = x + (int64_t)(rh0 + k) * ld;
+#pragma unroll
+              for (int u = 0; u < CW; ++u)
+                if (w0 + u < W) acc[k] += av[u] * (Acc)xr[jv[u]];
+            }
+          }
         }
       }
     }
@@ -469,7 +483,43 @@ int spmm_tuned_ws(const bem_operator* op, int nrhs, int arith) {
   return it == g_tuned.end() ? 0 : it->second;
 }
 
+// NR right-hand sides per pass over the values (1: the single-vector kernel,
+// with fewer registers)
+template <int NR>
+static bem_status spmv_launch(const bem_operator* op, const double* x, double* y, int nrhs, int arith, int threads,
+                              int groups, cudaStream_t s) {
+  const bem_mesh* m = op->mesh;
+  const int64_t n = m->n_tet;
+  const size_t smem = sizeof(double) * threads * NR;
+  if (arith == MV_FP32) {
+    if (!op->d_val32) {
+      set_error("operator has no FP32 values (store_fp32 = 0)");
+      return BEM_ERR_INVALID_ARG;
+    }
+    bem_status st = ensure_ws(op, n * nrhs);
+    if (st != BEM_OK) return st;
+    k_to_f32<<<grid_for(n * nrhs), 256, 0, s>>>(x, op->d_ws, n * nrhs);
+    k_matvec<float, float, float, NR><<<(unsigned)m->n_col, threads, smem, s>>>(
+        m->n_col, m->d_col_tet_begin, op->d_bw, op->d_boff, op->d_rsoff, op->d_rs, op->d_val32, op->d_ws, y, n,
+        nrhs, groups);
+  } else if (op->d_val) {
+    k_matvec<double, double, double, NR><<<(unsigned)m->n_col, threads, smem, s>>>(
+        m->n_col, m->d_col_tet_begin, op->d_bw, op->d_boff, op->d_rsoff, op->d_rs, op->d_val, x, y, n, nrhs,
+        groups);
+  } else {
+    // mixed-precision operators keep FP32 values only
+    k_matvec<float, double, double, NR><<<(unsigned)m->n_col, threads, smem, s>>>(
+        m->n_col, m->d_col_tet_begin, op->d_bw, op->d_boff, op->d_rsoff, op->d_rs, op->d_val32, x, y, n, nrhs,
+        groups);
+  }
+  STBEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+
 bem_status op_matvec(const bem_operator* op, const double* x, double* y, int nrhs, int arith, cudaStream_t s) {
+  // matrix-free operators: the operator's own precision, whatever `arith` asks
+  if (op->opts.matrix_free) return op_matvec_free(op, x, y, nrhs, s);
   const bem_mesh* m = op->mesh;
   const int64_t n = m->n_tet;
   if (arith == MV_TF32 || arith == MV_BF16) {
@@ -518,31 +568,8 @@ bem_status op_matvec(const bem_operator* op, const double* x, double* y, int nrh
   const int rows_pad = ((m->max_col_tets + 31) / 32) * 32;
   const int groups = std::max(1, std::min(8, 512 / rows_pad));
   const int threads = rows_pad * groups;
-  constexpr int NR = 4;
-  const size_t smem = sizeof(double) * threads * NR;
-  if (arith == MV_FP32) {
-    if (!op->d_val32) {
-      set_error("operator has no FP32 values (store_fp32 = 0)");
-      return BEM_ERR_INVALID_ARG;
-    }
-    bem_status st = ensure_ws(op, n * nrhs);
-    if (st != BEM_OK) return st;
-    k_to_f32<<<grid_for(n * nrhs), 256, 0, s>>>(x, op->d_ws, n * nrhs);
-    k_matvec<float, float, float, NR><<<(unsigned)m->n_col, threads, smem, s>>>(
-        m->n_col, m->d_col_tet_begin, op->d_bw, op->d_boff, op->d_rsoff, op->d_rs, op->d_val32, op->d_ws, y, n,
-        nrhs, groups);
-  } else if (op->d_val) {
-    k_matvec<double, double, double, NR><<<(unsigned)m->n_col, threads, smem, s>>>(
-        m->n_col, m->d_col_tet_begin, op->d_bw, op->d_boff, op->d_rsoff, op->d_rs, op->d_val, x, y, n, nrhs,
-        groups);
-  } else {
-    // mixed-precision operators keep FP32 values only
-    k_matvec<float, double, double, NR><<<(unsigned)m->n_col, threads, smem, s>>>(
-        m->n_col, m->d_col_tet_begin, op->d_bw, op->d_boff, op->d_rsoff, op->d_rs, op->d_val32, x, y, n, nrhs,
-        groups);
-  }
-  STBEM_CUDA(cudaGetLastError());
-  return BEM_OK;
+  if (nrhs == 1) return spmv_launch<1>(op, x, y, nrhs, arith, threads, groups, s);
+  return spmv_launch<4>(op, x, y, nrhs, arith, threads, groups, s);
 }
 
 bem_status BatchMatvec::init(const std::vector<bem_operator*>& o, cudaStream_t s) {

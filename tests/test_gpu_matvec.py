@@ -98,3 +98,28 @@ def test_c2_spmm_64_dense(c2, dtype):
     rel = ((y - ref).norm(dim=1) / ref.norm(dim=1)).max().item()
     print("C2 64-RHS %s product, largest per-RHS relative 2-norm error: %.3e" % (dtype, rel))
     assert rel <= {"fp32": 1e-5, "tf32": 4e-3, "bf16": 3e-2}[dtype]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-12)])
+def test_matrix_free_product_matches_assembled(ctx, precision, tol):
+    """The matrix-free product (quadrature summed against x, no stored values)
+    against the assembled operator's FP64-accumulated product: the same
+    entries, so equal up to summation order."""
+    import paper_2103_16841_gb300 as stb
+    m = inputs.sphere_mesh(1, 8, 4.0, 0.2, seed=6)
+    mesh = stb.Mesh.from_spacetime(ctx, m)
+    op = stb.Operator(ctx, mesh, precision)
+    mf = stb.Operator(ctx, mesh, precision, matrix_free=True)
+    assert mf.stats()["nnz"] == op.stats()["nnz"] and mf.stats()["stored"] == 0
+    x = torch.tensor(np.random.default_rng(3).normal(size=(3, m.n_tet)), device="cuda")
+    y = op.matvec(x, dtype="fp64")
+    yf = mf.matvec(x)
+    err = ((yf - y).abs().max() / y.abs().max()).item()
+    print("matrix-free vs assembled (%s): %.3e" % (precision, err))
+    assert err <= tol
+    # a solve through the matrix-free operator
+    b = op.rhs(stb.DATA_PULSE, inputs.pulse_params(1, seed=2))[:, 0]
+    w, info = op.solve(b, tol=1e-10, restart=50, maxit=1000)
+    wf, infof = mf.solve(b, tol=1e-10, restart=50, maxit=1000)
+    assert infof[0]["converged"]
+    assert np.abs(wf - w).max() <= 1e-8 * np.abs(w).max()
