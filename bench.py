@@ -313,6 +313,25 @@ def multi_rhs_leg(op, m, args):
     out = {"nrhs": nrhs, "pulses": "exp(-((t - x.d - c)/0.25)^2), d seeded unit vectors, c ~ U[1, 2]",
            "products": {}, "solves": {}}
     stream = torch.cuda.Stream()
+    hbm = peaks().get("hbm_gbs")
+    # one vector, FP32 values (the inner-solve product): HBM-bound
+    x1 = x[:1].contiguous()
+    y1 = op.matvec(x1, dtype="fp32", stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(10):
+        e0.record(stream)
+        op.matvec(x1, y1, dtype="fp32", stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms1 = float(np.median(ts))
+    gbs1 = st["stored"] * 4 / (ms1 / 1e3) / 1e9
+    out["products"]["fp32_x1"] = {"ms": round(ms1, 3), "value_GBps": round(gbs1, 1),
+                                  "frac_of_measured_hbm": round(gbs1 / hbm, 3) if hbm else None,
+                                  "note": "4 B per stored value over the call (conversions and permutations "
+                                          "included), against the measured HBM copy bandwidth"}
     for dt in ["fp32", "tf32", "bf16"]:
         y = op.matvec(x, dtype=dt, stream=stream)          # first call: workspace, autotune
         reps = 5
@@ -329,6 +348,7 @@ def multi_rhs_leg(op, m, args):
         vbytes = st["stored"] * (2 if dt == "bf16" else 4)
         out["products"][dt] = {"ms": round(ms, 3), "value_bytes": vbytes,
                                "value_GBps": round(vbytes / (ms / 1e3) / 1e9, 1),
+                               "frac_of_measured_hbm": round(vbytes / (ms / 1e3) / 1e9 / hbm, 3) if hbm else None,
                                "passes_over_values": math.ceil(nrhs / 4) if dt == "fp32" else math.ceil(nrhs / 64),
                                "note": "includes the FP64 <-> packed-operand conversions and the caller-order "
                                        "permutations of bem_matvec_dtype"}
