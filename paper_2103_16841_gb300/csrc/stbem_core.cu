@@ -483,6 +483,10 @@ __global__ void __launch_bounds__(128) k_pattern_batch(const BlockCtx* __restric
   }
 }
 
+// shared bytes per warp for the deferred arcs of the mixed kernel
+constexpr size_t ARC_WARP_BYTES = 96 * sizeof(ArcRec<float>) + 96 * sizeof(float) + 96;
+static_assert(ARC_WARP_BYTES % 16 == 0, "arc region keeps 16-byte alignment");
+
 // Pass 2: quadrature and assembly of a non-empty block.
 template <bool FP32>
 __device__ __forceinline__ void quad_block(const BlockCtx& B, int64_t b, unsigned char* smem, ColSm& C,
@@ -500,6 +504,12 @@ __device__ __forceinline__ void quad_block(const BlockCtx& B, int64_t b, unsigne
   uint16_t* cut0 = reinterpret_cast<uint16_t*>(Wsc0 + (size_t)nw * B.nq * B.max_surf);
   uint16_t* mycut = cut0 + (size_t)warp * B.nq * B.max_surf;
   FaceF* Ff = reinterpret_cast<FaceF*>(cut0 + ((size_t)nw * B.nq * B.max_surf + 7) / 8 * 8);
+  // mixed: per warp 96 deferred arcs (3 per lane), their values and the compacted order
+  unsigned char* arc0 = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(Ff + B.max_surf) + 15) & ~static_cast<uintptr_t>(15));
+  ArcRec<float>* myarc = reinterpret_cast<ArcRec<float>*>(arc0 + (size_t)warp * ARC_WARP_BYTES);
+  float* myval = reinterpret_cast<float*>(myarc + 96);
+  uint8_t* myidx = reinterpret_cast<uint8_t*>(myval + 96);
   R* U = reinterpret_cast<R*>(B.uscratch) + (size_t)blockIdx.x * B.max_surf * B.max_tet;
   {
     int W = B.bw[b];
@@ -564,6 +574,47 @@ __device__ __forceinline__ void quad_block(const BlockCtx& B, int64_t b, unsigne
       }
       __syncwarp();
       // pass 2: the cut pairs, converged across the warp
+      if constexpr (FP32) {
+        // mixed: the geometry and edge pieces lane per cut pair; the conic
+        // arcs they need (at most 3 per pair, two thirds of the work) are
+        // collected and integrated lane per arc over the compacted list, then
+        // each pair adds its arcs in order (the same sum as in face_cut)
+        for (int base = 0; base < ncut; base += 32) {
+          const int k = base + lane;
+          int na = 0, q = 0, s = 0;
+          float et = 0.f;
+          if (k < ncut) {
+            const int it = mycut[k];
+            q = it / nsw;
+            s = it - q * nsw;
+            float Fv[3], cc = 0.f;
+            face_class_mixed(mypc[q], Ff[slo + s], Fv, cc, fdiam);
+            FaceCutIn<float> in;
+            cut_in_mixed(mypc[q], Ff[slo + s], Fv, cc, Fs[slo + s], in);
+            et = (float)face_cut<float>(CR, mypc[q], in, B.rule, myarc + 3 * lane, &na);
+          }
+          int incl = na;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+          }
+          const int off = incl - na, total = __shfl_sync(0xffffffffu, incl, 31);
+          for (int i = 0; i < na; ++i) myidx[off + i] = (uint8_t)(3 * lane + i);
+          __syncwarp();
+          for (int a = lane; a < total; a += 32) {
+            const int slot = myidx[a];
+            myval[slot] = arc_value<float>(myarc[slot], B.rule);
+          }
+          __syncwarp();
+          if (k < ncut) {
+            float v = et;
+            for (int i = 0; i < na; ++i) v += myval[3 * lane + i];
+            Wsc[q * B.max_surf + s] = v;
+          }
+          __syncwarp();
+        }
+      } else
       for (int k = lane; k < ncut; k += 32) {
         int it = mycut[k];
         int q = it / nsw, s = it - q * nsw;
@@ -690,6 +741,7 @@ static size_t block_smem(const bem_operator* op, bool quad) {
     s += (op->opts.precision == BEM_PREC_MIXED ? sizeof(float) : sizeof(double)) * 4 * op->nq * m->max_col_surf;
     s += sizeof(uint16_t) * (((size_t)4 * op->nq * m->max_col_surf + 7) / 8 * 8);
     s += sizeof(FaceF) * m->max_col_surf;
+    if (op->opts.precision == BEM_PREC_MIXED) s += 16 + 4 * ARC_WARP_BYTES;
   }
   return s;
 }
@@ -820,6 +872,7 @@ static size_t batch_smem(int max_tet, int max_surf, int nq, bool quad, bool fp32
     s += (fp32 ? sizeof(float) : sizeof(double)) * 4 * nq * max_surf;
     s += sizeof(uint16_t) * (((size_t)4 * nq * max_surf + 7) / 8 * 8);
     s += sizeof(FaceF) * max_surf;
+    if (fp32) s += 16 + 4 * ARC_WARP_BYTES;
   }
   return s;
 }

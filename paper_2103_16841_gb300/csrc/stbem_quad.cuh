@@ -722,9 +722,27 @@ STBEM_HD inline void cut_in_mixed(const PointCol& P, const FaceF& Fc, const floa
   o.c64 = (double)c;
 }
 
+// A conic arc of a cut face (d != 0) recorded for evaluation later: the
+// quadrature kernel collects the arcs of all cut pairs of a warp and then
+// integrates them one per lane over the compacted list.
+template <typename R>
+struct ArcRec {
+  R A[2], dAB[2], c, d, g[2];
+  int full;
+};
+
+template <typename R>
+STBEM_HD inline R arc_value(const ArcRec<R>& a, const ArcRule& rule) {
+  return conic_arc<R>(a.full ? nullptr : a.A, a.full ? nullptr : a.dAB, a.full != 0, a.c, a.d, a.g, rule, 0.0,
+                      nullptr);
+}
+
+// 4 pi W_P(x) of a cut face. With `defer` given, arcs with d != 0 (at most
+// three) are appended to defer[*ndefer] instead of integrated, and the
+// return value holds the edge pieces (and any coplanar arc) only.
 template <typename R>
 STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, const FaceCutIn<R>& in,
-                                      const ArcRule& rule) {
+                                      const ArcRule& rule, ArcRec<R>* defer = nullptr, int* ndefer = nullptr) {
   const PtR<R>& P = pt<R>(P64);
   const R d = P.d, c = in.c;
   const R* g = in.g;
@@ -800,7 +818,13 @@ STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, con
         int j = (i + s) % nev;
         if (ev_in[j]) {
           R dAB[2] = {ev_l[j][0] - ev_l[i][0], ev_l[j][1] - ev_l[i][1]};
-          total += conic_arc<R>(ev_y[i], dAB, false, c, d, g, rule, in.c64, in.g64);
+          if (defer && d != R(0)) {
+            ArcRec<R>& a = defer[(*ndefer)++];
+            a.A[0] = ev_y[i][0]; a.A[1] = ev_y[i][1]; a.dAB[0] = dAB[0]; a.dAB[1] = dAB[1];
+            a.c = c; a.d = d; a.g[0] = g[0]; a.g[1] = g[1]; a.full = 0;
+          } else {
+            total += conic_arc<R>(ev_y[i], dAB, false, c, d, g, rule, in.c64, in.g64);
+          }
           break;
         }
       }
@@ -816,7 +840,13 @@ STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, con
       R rel[2] = {yst[0] - P.q[k][0], yst[1] - P.q[k][1]};
       if (!(G.U[k][0] * rel[1] - G.U[k][1] * rel[0] > R(0))) return 0.0;
     }
-    total += conic_arc<R>(nullptr, nullptr, true, c, d, g, rule, in.c64, in.g64);
+    if (defer && d != R(0)) {
+      ArcRec<R>& a = defer[(*ndefer)++];
+      a.A[0] = a.A[1] = a.dAB[0] = a.dAB[1] = R(0);
+      a.c = c; a.d = d; a.g[0] = g[0]; a.g[1] = g[1]; a.full = 1;
+    } else {
+      total += conic_arc<R>(nullptr, nullptr, true, c, d, g, rule, in.c64, in.g64);
+    }
   }
   return (double)total;
 }
