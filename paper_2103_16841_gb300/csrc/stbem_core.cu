@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "stbem_internal.h"
@@ -610,6 +612,8 @@ __device__ __forceinline__ void quad_block(const BlockCtx& B, int64_t b, unsigne
           if (k < ncut) {
             float v = et;
             for (int i = 0; i < na; ++i) v += myval[3 * lane + i];
+            if (!isfinite(v))   // degenerate FP32 geometry: this face in FP64
+              v = (float)face_W_fp64(P + 4 * q, C.G, Fs[slo + s], B.n_theta);
             Wsc[q * B.max_surf + s] = v;
           }
           __syncwarp();
@@ -746,6 +750,23 @@ static size_t block_smem(const bem_operator* op, bool quad) {
   return s;
 }
 
+// The dynamic shared-memory limit of a kernel is state of the device shared by
+// every host thread: operators of different sizes launching the same kernel
+// concurrently (server slots) must never lower it under another's launch, so
+// it only grows, under a lock.
+bem_status ensure_smem_attr(const void* kern, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> set_to;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = set_to[std::make_pair(dev, kern)];
+  if (bytes <= cur) return BEM_OK;
+  STBEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  cur = bytes;
+  return BEM_OK;
+}
+
 static int persistent_grid(const void* kern, size_t smem, int threads) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
@@ -784,7 +805,8 @@ bem_status op_pattern(bem_operator* op, cudaStream_t s) {
   bem_status st = get_counter(op, &B.counter, s);
   if (st != BEM_OK) return st;
   size_t smem = block_smem(op, false);
-  STBEM_CUDA(cudaFuncSetAttribute(k_pattern_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  st = ensure_smem_attr((const void*)k_pattern_blocks, smem);
+  if (st != BEM_OK) return st;
   int grid = persistent_grid((const void*)k_pattern_blocks, smem, 128);
   k_pattern_blocks<<<grid, 128, smem, s>>>(B);
   STBEM_CUDA(cudaGetLastError());
@@ -794,10 +816,10 @@ bem_status op_pattern(bem_operator* op, cudaStream_t s) {
 int quad_grid(const bem_operator* op) {
   size_t smem = block_smem(op, true);
   if (op->opts.precision == BEM_PREC_MIXED) {
-    cudaFuncSetAttribute(k_quad_blocks<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    ensure_smem_attr((const void*)k_quad_blocks<true>, smem);
     return persistent_grid((const void*)k_quad_blocks<true>, smem, 128);
   }
-  cudaFuncSetAttribute(k_quad_blocks<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  ensure_smem_attr((const void*)k_quad_blocks<false>, smem);
   return persistent_grid((const void*)k_quad_blocks<false>, smem, 128);
 }
 
@@ -904,7 +926,8 @@ bem_status op_pattern_batch(const std::vector<bem_operator*>& ops, BatchDev& dev
   bem_status st = upload_batch(ops, dev, mt, ms, s);
   if (st != BEM_OK) return st;
   const size_t smem = batch_smem(mt, ms, ops[0]->nq, false);
-  STBEM_CUDA(cudaFuncSetAttribute(k_pattern_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  st = ensure_smem_attr((const void*)k_pattern_batch, smem);
+  if (st != BEM_OK) return st;
   const int grid = persistent_grid((const void*)k_pattern_batch, smem, 128);
   k_pattern_batch<<<grid, 128, smem, s>>>(static_cast<const BlockCtx*>(dev.d_ctx), dev.d_prefix, (int)ops.size(),
                                           dev.d_counter);
@@ -917,10 +940,10 @@ static int quad_batch_grid(const std::vector<bem_operator*>& ops, size_t& smem) 
   batch_dims(ops, mt, ms);
   smem = batch_smem(mt, ms, ops[0]->nq, true, ops[0]->opts.precision == BEM_PREC_MIXED);
   if (ops[0]->opts.precision == BEM_PREC_MIXED) {
-    cudaFuncSetAttribute(k_quad_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    ensure_smem_attr((const void*)k_quad_batch<true>, smem);
     return persistent_grid((const void*)k_quad_batch<true>, smem, 128);
   }
-  cudaFuncSetAttribute(k_quad_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  ensure_smem_attr((const void*)k_quad_batch<false>, smem);
   return persistent_grid((const void*)k_quad_batch<false>, smem, 128);
 }
 
@@ -1093,7 +1116,10 @@ bem_status op_pattern_csr(const bem_operator* op, int64_t* d_rowcount, int64_t* 
   bem_status st = get_counter(op, &B.counter, s);
   if (st != BEM_OK) return st;
   size_t smem = block_smem(op, false);
-  STBEM_CUDA(cudaFuncSetAttribute(k_pattern_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    bem_status sa = ensure_smem_attr((const void*)k_pattern_rows, smem);
+    if (sa != BEM_OK) return sa;
+  }
   int grid = persistent_grid((const void*)k_pattern_rows, smem, 128);
   k_pattern_rows<<<grid, 128, smem, s>>>(B, d_rowcount, d_rowptr, d_cols, fill ? 1 : 0, I_only);
   STBEM_CUDA(cudaGetLastError());
@@ -1218,6 +1244,8 @@ __global__ void k_inner(int64_t n, const double* x4, const double* tv, const int
   point_col(x4 + 4 * k, G, P, FP32);
   const ArcRule rule = make_rule(FP32 ? BEM_PREC_MIXED : BEM_PREC_FP64, n_theta);
   double wl = face_W<FP32>(G, P, Flo, rule), wh = face_W<FP32>(G, P, Fhi, rule);
+  if (FP32 && !isfinite(wl)) wl = face_W_fp64(x4 + 4 * k, G, Flo, n_theta);
+  if (FP32 && !isfinite(wh)) wh = face_W_fp64(x4 + 4 * k, G, Fhi, n_theta);
   out[k] = (wl - wh) / (4.0 * STBEM_PI);
 }
 

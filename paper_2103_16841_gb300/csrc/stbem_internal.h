@@ -109,6 +109,8 @@ bem_status mesh_device_geometry(bem_mesh* m, const double* d_sv_xyz, const int32
 bem_status op_outer_points(bem_operator* op, cudaStream_t s);
 bem_status op_pattern(bem_operator* op, cudaStream_t s);
 bem_status op_quadrature(bem_operator* op, cudaStream_t s);
+// raise a kernel's dynamic shared-memory limit to at least `bytes` (never lowers it)
+bem_status ensure_smem_attr(const void* kern, size_t bytes);
 // matrix-free product (internal order): the quadrature pass summed against x
 bem_status op_matvec_free(const bem_operator* op, const double* x, double* y, int nrhs, cudaStream_t s);
 // Layout of the vectors of a batched GMRES: K vectors of length N ([K][N]);

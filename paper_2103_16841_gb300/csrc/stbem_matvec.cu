@@ -399,7 +399,10 @@ bem_status launch_spmm_ws(const SpmmArgs& a, cudaStream_t s) {
   const int threads = a.strips * WS * 32;
   const size_t smem = WS > 1 ? sizeof(float) * (size_t)(WS - 1) * a.strips * NT8 * 4 * 32 : 0;
   if (smem > 48 * 1024)
-    STBEM_CUDA(cudaFuncSetAttribute(k_spmm<BF16, NT8, WS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+      bem_status sa = ensure_smem_attr((const void*)k_spmm<BF16, NT8, WS>, smem);
+      if (sa != BEM_OK) return sa;
+    }
   k_spmm<BF16, NT8, WS><<<(unsigned)a.n_col, threads, smem, s>>>(a);
   STBEM_CUDA(cudaGetLastError());
   return BEM_OK;

@@ -586,6 +586,10 @@ STBEM_HD __noinline__ R conic_arc(const R* A, const R* dAB, bool full, R c, R d,
   if (full) span = twopi;
   else {
     R dth = arc_dtheta<R>(F, A, dAB);
+    // FP32: when the two events are as close as their rounding (the cone
+    // grazing a corner), the span cannot tell a vanishing arc from a full
+    // turn; NaN asks the caller to recompute the face in FP64
+    if (sizeof(R) == 4 && !(fabs(dth) >= R(1e-5))) return (R)nan("");
     span = s > R(0) ? dth : -dth;
     if (span < R(0)) span += twopi;
   }
@@ -885,6 +889,14 @@ STBEM_HD inline double face_W(const ColGeom& G, const PointCol& P, const FaceGeo
   FaceCutIn<double> in;
   cut_in_fp64(P, Fc, F, c, in);
   return face_cut<double>(CR, P, in, rule);
+}
+
+// 4 pi W_P(x) entirely in FP64 from the apex coordinates: the fallback of the
+// mixed path for faces whose FP32 evaluation is not finite (see conic_arc)
+STBEM_HD __noinline__ inline double face_W_fp64(const double* x, const ColGeom& G, const FaceGeom& Fc, int n_theta) {
+  PointCol P;
+  point_col(x, G, P, false);
+  return face_W<false>(G, P, Fc, make_rule(0, n_theta));
 }
 
 }  // namespace stbem

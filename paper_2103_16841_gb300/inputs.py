@@ -209,12 +209,14 @@ def workload_c2(seed=1):
     return sphere_mesh(3, 32, 4.0, 0.2, seed)
 
 
-def scatterer_meshes(n, T=4.0, jitter=0.2, seed=3):
+def scatterer_meshes(n, T=4.0, jitter=0.2, seed=3, only=None):
     """Space-time meshes and pulse parameters of n small ellipsoid scatterers
     (icosphere level 1 or 2 scaled by semi-axes in [0.5, 1.5], 8-16 slabs,
-    1-4 pulse right-hand sides each)."""
+    1-4 pulse right-hand sides each); `only`: the indices to build."""
     out = []
     for k, (level, axes, slabs, nrhs) in enumerate(small_scatterers(n, seed)):
+        if only is not None and k not in only:
+            continue
         v, f = ellipsoid(level, axes)
         m = prism_mesh(v, f, slabs, T, jitter, seed=seed * 100003 + k)
         out.append((m, pulse_params(nrhs, seed=seed * 100019 + k)))
