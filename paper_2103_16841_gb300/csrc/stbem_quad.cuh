@@ -554,7 +554,7 @@ STBEM_HD __noinline__ R arc_d0(const R* A, const R* dAB, bool full, R c, const R
 // that short arcs far from xb keep their relative accuracy.
 template <typename R>
 STBEM_HD __noinline__ R conic_arc(const R* A, const R* dAB, bool full, R c, R d, const R* g, const ArcRule& rule,
-                                  double c64, const double* g64) {
+                                  double c64, const double* g64, bool tiny_is_short = false) {
   if (d == R(0)) {
     // closed form in FP64 in every precision: it is a difference of
     // antiderivative values, and it only arises for coplanar pairs
@@ -586,12 +586,18 @@ STBEM_HD __noinline__ R conic_arc(const R* A, const R* dAB, bool full, R c, R d,
   if (full) span = twopi;
   else {
     R dth = arc_dtheta<R>(F, A, dAB);
-    // FP32: when the two events are as close as their rounding (the cone
-    // grazing a corner), the span cannot tell a vanishing arc from a full
-    // turn; NaN asks the caller to recompute the face in FP64
-    if (sizeof(R) == 4 && !(fabs(dth) >= R(1e-5))) return (R)nan("");
-    span = s > R(0) ? dth : -dth;
-    if (span < R(0)) span += twopi;
+    if (sizeof(R) == 4 && !(fabs(dth) >= R(1e-5))) {
+      // FP32: the two events are as close as their rounding (the cone grazing
+      // a corner), so the sign of the span cannot tell a vanishing arc from a
+      // full turn. Where the lit set cannot be a whole ellipse inside the
+      // triangle (tiny_is_short) the arc is the short one; otherwise NaN asks
+      // the caller to recompute the face in FP64.
+      if (!tiny_is_short) return (R)nan("");
+      span = fabs(dth);
+    } else {
+      span = s > R(0) ? dth : -dth;
+      if (span < R(0)) span += twopi;
+    }
   }
   R lo = s > R(0) ? thA : thA - span;
   R hi = s > R(0) ? thA + span : thA;
@@ -732,13 +738,13 @@ STBEM_HD inline void cut_in_mixed(const PointCol& P, const FaceF& Fc, const floa
 template <typename R>
 struct ArcRec {
   R A[2], dAB[2], c, d, g[2];
-  int full;
+  int full, tiny_is_short;
 };
 
 template <typename R>
 STBEM_HD inline R arc_value(const ArcRec<R>& a, const ArcRule& rule) {
   return conic_arc<R>(a.full ? nullptr : a.A, a.full ? nullptr : a.dAB, a.full != 0, a.c, a.d, a.g, rule, 0.0,
-                      nullptr);
+                      nullptr, a.tiny_is_short != 0);
 }
 
 // 4 pi W_P(x) of a cut face. With `defer` given, arcs with d != 0 (at most
@@ -814,6 +820,9 @@ STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, con
       ++nev;
     }
   }
+  // the lit set is a whole ellipse inside K only if the conic is bounded and
+  // narrower than K (its width across g is at least 2 sqrt(c^2 - d^2))
+  const bool tiny_short = (g[0] * g[0] + g[1] * g[1] >= R(1)) || (c * c - d * d > R(0.25) * G.diam * G.diam);
   if (nev > 0) {
     // events are in perimeter order; each exit connects to the next entry
     for (int i = 0; i < nev; ++i) {
@@ -825,9 +834,9 @@ STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, con
           if (defer && d != R(0)) {
             ArcRec<R>& a = defer[(*ndefer)++];
             a.A[0] = ev_y[i][0]; a.A[1] = ev_y[i][1]; a.dAB[0] = dAB[0]; a.dAB[1] = dAB[1];
-            a.c = c; a.d = d; a.g[0] = g[0]; a.g[1] = g[1]; a.full = 0;
+            a.c = c; a.d = d; a.g[0] = g[0]; a.g[1] = g[1]; a.full = 0; a.tiny_is_short = tiny_short;
           } else {
-            total += conic_arc<R>(ev_y[i], dAB, false, c, d, g, rule, in.c64, in.g64);
+            total += conic_arc<R>(ev_y[i], dAB, false, c, d, g, rule, in.c64, in.g64, tiny_short);
           }
           break;
         }
@@ -847,7 +856,7 @@ STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, con
     if (defer && d != R(0)) {
       ArcRec<R>& a = defer[(*ndefer)++];
       a.A[0] = a.A[1] = a.dAB[0] = a.dAB[1] = R(0);
-      a.c = c; a.d = d; a.g[0] = g[0]; a.g[1] = g[1]; a.full = 1;
+      a.c = c; a.d = d; a.g[0] = g[0]; a.g[1] = g[1]; a.full = 1; a.tiny_is_short = 0;
     } else {
       total += conic_arc<R>(nullptr, nullptr, true, c, d, g, rule, in.c64, in.g64);
     }
