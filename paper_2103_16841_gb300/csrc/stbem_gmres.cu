@@ -98,7 +98,6 @@ __global__ void k_combine(const double* __restrict__ V, int64_t ldv, const doubl
 
 struct GState {
   int* j;            // current step
-  int* one;          // constant 1 (vector count of the norm reductions)
   int* nactive;
   double* H;         // [C][(m+1) m] column-major Hessenberg per column
   double* g;         // [C][m+1]
@@ -355,10 +354,8 @@ bem_status gmres_device(const SegLayout& L, const MatvecFn& mv, const double* d_
   G_TRY(active.alloc(C, true, s));
   G_TRY(kdim.alloc(C, true, s));
   G_TRY(it.alloc(C, true, s));
-  GState G{ints.p, ints.p + 1, ints.p + 2, H.p, g.p, cs.p, sn.p, h1.p, h2.p, hn2.p, bnorm.p, rel.p, scale.p, y.p,
+  GState G{ints.p, ints.p + 2, H.p, g.p, cs.p, sn.p, h1.p, h2.p, hn2.p, bnorm.p, rel.p, scale.p, y.p,
            active.p, kdim.p, it.p};
-  const int one = 1;
-  STBEM_CUDA(cudaMemcpyAsync(G.one, &one, sizeof(int), cudaMemcpyHostToDevice, s));
   const unsigned gN = grid_of(NN), gC = (unsigned)((C + 63) / 64);
   auto norms2 = [&](const double* v, double* out) -> bem_status {
     k_dot_partial<<<(unsigned)n_items, TPB, 0, s>>>(v, 0, nullptr, 1, v, it_st_p, it_ln_p, n_items, partial.p);

@@ -179,8 +179,6 @@ int64_t operator_value_bytes(const bem_operator* op);
 // arithmetic of a product (values equal to BEM_DTYPE_*)
 enum { MV_FP64 = 0, MV_FP32 = 1, MV_TF32 = 2, MV_BF16 = 3 };
 bem_status op_matvec(const bem_operator* op, const double* x, double* y, int nrhs, int arith, cudaStream_t s);
-// warps per strip the SpMM autotuner picked for this operator's shape (0: not yet tuned)
-int spmm_tuned_ws(const bem_operator* op, int nrhs, int arith);
 bem_status op_rhs(const bem_operator* op, int kind, int nrhs, const double* d_params, double* d_b, cudaStream_t s);
 bem_status op_value_scan(const bem_operator* op, int64_t* nbad, double* maxabs, cudaStream_t s);
 bem_status op_entries(const bem_operator* op, int64_t n, const int32_t* d_ij, double* d_out, cudaStream_t s);

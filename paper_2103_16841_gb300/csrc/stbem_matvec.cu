@@ -478,14 +478,6 @@ bem_status spmm_nt8(const bem_operator* op, const SpmmArgs& a, int nt8, cudaStre
 
 }  // namespace
 
-int spmm_tuned_ws(const bem_operator* op, int nrhs, int arith) {
-  int nt8 = nrhs <= 8 ? 1 : nrhs <= 16 ? 2 : nrhs <= 32 ? 4 : 8;
-  std::lock_guard<std::mutex> lk(g_tune_mu);
-  auto it = g_tuned.find(std::make_tuple(op->mesh->n_col, op->mesh->max_col_tets, nt8, (int)(arith == MV_BF16),
-                                         op->ctx->device));
-  return it == g_tuned.end() ? 0 : it->second;
-}
-
 // NR right-hand sides per pass over the values (1: the single-vector kernel,
 // with fewer registers)
 template <int NR>
