@@ -459,17 +459,36 @@ STBEM_HD __noinline__ R arc_piece(const ArcFrame<R>& F, R lo, R hi, const ArcRul
   R mid = R(0.5) * (lo + hi), half = R(0.5) * (hi - lo);
   if (!(half > R(0))) return R(0);
   R best_rho = R(1e30), best_a = R(0), best_b = R(1e30);
+  R sm, cm;
+  sc(mid, &sm, &cm);
   {
     // poles of I: L1 = 1 - <g, n_par> = 0 (r -> infinity) and
-    // r + |d| = 0, i.e. L1 = -c / |d| (complex for the valid arc)
+    // r + |d| = 0, i.e. L1 = -c / |d| (complex for the valid arc). Both are
+    // zeros of f = A0 - A1 cos(theta - theta1); since |f(z) - f(mid)| <=
+    // A1 sinh|z - mid|, f has no zero within asinh(|f(mid)| / A1) of mid.
+    // In FP32, when that disk holds a Bernstein ellipse of the piece with
+    // parameter >= 16 (the minimum order already reaches the tolerance there),
+    // the exact pole location cannot change the rule and is skipped.
     R gw = F.g[0] * F.wh[0] + F.g[1] * F.wh[1];
     R ga = F.g[0] * F.ea[0] + F.g[1] * F.ea[1];
     R gb = F.g[0] * F.eb[0] + F.g[1] * F.eb[1];
-    consider_pole<R>(R(1) - F.ca * gw, F.sa * ga, F.sa * gb, mid, half, best_rho, best_a, best_b);
-    consider_pole<R>(R(1) + F.c / fabs(F.d) - F.ca * gw, F.sa * ga, F.sa * gb, mid, half, best_rho, best_a, best_b);
+    bool far_poles = false;
+    if (sizeof(R) == 4) {
+      const R Aa = F.sa * ga, Ab = F.sa * gb;
+      const R A1 = sqrt(Aa * Aa + Ab * Ab);
+      const R f1 = (R(1) - F.ca * gw) - (Aa * cm + Ab * sm);
+      const R f2 = f1 + F.c / fabs(F.d);
+      const R fm = fmin(fabs(f1), fabs(f2));
+      far_poles = !(A1 > R(0)) || R(2) * asinh(fm / A1) >= R(16) * half;
+      // Gauss error ~ R^(-2n): R >= 15.9 and n_min >= 4 reach 15.9^-6 < 1/1.6e7
+      far_poles = far_poles && rule.nmin >= 4 && rule.tol >= 1.0 / 1.6e7;
+    }
+    if (!far_poles) {
+      consider_pole<R>(R(1) - F.ca * gw, F.sa * ga, F.sa * gb, mid, half, best_rho, best_a, best_b);
+      consider_pole<R>(R(1) + F.c / fabs(F.d) - F.ca * gw, F.sa * ga, F.sa * gb, mid, half, best_rho, best_a,
+                       best_b);
+    }
   }
-  R sm, cm;
-  sc(mid, &sm, &cm);
   ArcEval<R> E;
   E.ca = F.ca; E.sa = F.sa;
   for (int i = 0; i < 3; ++i) {
