@@ -688,10 +688,10 @@ __device__ __forceinline__ void quad_block(const BlockCtx& B, int64_t b, unsigne
 }
 
 // CTAs of 128 threads resident per SM that the register budget is cut for
-// (timed on the level-3, 16-slab sphere: 3 / 4 / 5 CTAs gave 95 / 103 / 111
-// million pairs/s)
+// (quadrature of the level-3, 32-slab sphere in mixed precision: 4 / 5 / 6
+// CTAs took 6.83 / 6.91 / 7.56 s)
 #ifndef STBEM_QUAD_MIN_CTAS
-#define STBEM_QUAD_MIN_CTAS 5
+#define STBEM_QUAD_MIN_CTAS 4
 #endif
 
 template <bool FP32>
