@@ -229,9 +229,12 @@ bem_status bem_matvec_dtype(const bem_operator* op, const double* x_dev, double*
  * exceed 1,048,576 (BEM_ERR_INVALID_ARG otherwise). It calls no allocator.
  * The first call on a device looks up the array's device address (once per
  * device); make that first call before any stream capture. The call is
- * enqueued on `stream` and returns without synchronizing. All calls share the
+ * enqueued on `stream` and returns without synchronizing; the calling thread's
+ * current device is the same after the call as before it. All calls share the
  * array: calls whose work overlaps on the GPU (other streams, other threads)
- * race on it and must be ordered by the caller. */
+ * race on it and must be ordered by the caller. Matrix-free operators run
+ * their quadrature pass with the operator's own scratch, allocated when the
+ * operator was created. */
 bem_status bem_matvec_noalloc(const bem_operator* op, const double* x_dev, double* y_dev, int32_t nrhs, void* stream);
 
 /* ------------------------------------------------------------------ */

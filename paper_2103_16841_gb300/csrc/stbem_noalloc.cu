@@ -50,7 +50,14 @@ extern "C" bem_status bem_matvec_noalloc(const bem_operator* op, const double* x
     set_error("bem_matvec_noalloc: device index out of range");
     return BEM_ERR_INVALID_ARG;
   }
-  STBEM_CUDA(cudaSetDevice(dev));
+  // the caller's current device is put back before returning
+  int prev = -1;
+  STBEM_CUDA(cudaGetDevice(&prev));
+  if (prev != dev) STBEM_CUDA(cudaSetDevice(dev));
+  struct Restore {
+    int to, from;
+    ~Restore() { if (to != from) cudaSetDevice(to); }
+  } restore{prev, dev};
   double* base = nullptr;
   {
     // once per device, with that device current: the array's device address
