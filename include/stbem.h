@@ -44,7 +44,8 @@ typedef enum {
   BEM_ERR_DEVICE_TIMEOUT = 5,/* a bounded device wait gave up */
   BEM_ERR_UNSUPPORTED = 6,   /* option or mesh shape outside what is built */
   BEM_ERR_BAD_MESH = 7,      /* mesh fails validation (see bem_mesh_create) */
-  BEM_ERR_INTERNAL = 8
+  BEM_ERR_INTERNAL = 8,
+  BEM_ERR_CANCELLED = 9      /* an asynchronous solve was cancelled (bem_request_cancel) */
 } bem_status;
 
 typedef struct bem_context bem_context;
@@ -65,6 +66,11 @@ enum { BEM_PREC_FP64 = 0, BEM_PREC_MIXED = 1 };
  * BF16  tensor cores: values and x rounded to BF16, FP32 accumulation. */
 enum { BEM_DTYPE_FP64 = 0, BEM_DTYPE_FP32 = 1, BEM_DTYPE_TF32 = 2, BEM_DTYPE_BF16 = 3 };
 
+/* Trial space of the density (Def. st_be, Sec. 3): P0 = S_h^0, piecewise
+ * constant per panel (the space of eq. df_ind, built); P1 = V_h^1, continuous
+ * piecewise linear in space-time (not built: BEM_ERR_UNSUPPORTED). */
+enum { BEM_TRIAL_P0 = 0, BEM_TRIAL_P1 = 1 };
+
 /* Dirichlet data families (evaluated at space-time points (t, x)):
  *  BEM_DATA_SIN2_UNIFORM: g = sin^2(pi t / 2) for 0 < t < 2, else 0
  *                         (params ignored);
@@ -83,6 +89,15 @@ void bem_context_destroy(bem_context* ctx);
 /* Thread-local text of the last failure in this thread ("" if none). */
 const char* bem_last_error(void);
 const char* bem_version(void);
+
+/* Measured FMA throughput of the context's device at its present clocks, in
+ * TFLOP/s (2 flops per FMA lane): FP32 (the larger of scalar and paired
+ * FMAs) and FP64. Diagnostics with no counterpart in the paper: the
+ * light-cone quadrature is bound by these two pipes, and these rates are the
+ * denominators of its roofline. Register-resident FMA chains on every SM,
+ * each kernel timed with CUDA events at >= 50 ms per launch (about 1 s in
+ * all); synchronizes the context stream. */
+bem_status bem_alu_peaks(bem_context* ctx, double* fp32_tflops, double* fp64_tflops);
 
 /* ------------------------------------------------------------------ */
 /* Space-time mesh of Sigma (Sec. 3: Sigma_N of open tetrahedra)        */
@@ -133,6 +148,7 @@ typedef struct {
   int32_t matrix_free;/* 1: no values are stored; every product re-runs the quadrature with the
                         entries summed against x on the fly (the dot product fused into the
                         quadrature pass); export_dense / entries are then unsupported. */
+  int32_t trial_space;/* BEM_TRIAL_P0 (0, the default); BEM_TRIAL_P1 returns BEM_ERR_UNSUPPORTED */
 } bem_op_opts;
 
 /* Assembles the sparse Galerkin matrix on the device.
@@ -191,19 +207,49 @@ void bem_operator_destroy(bem_operator* op);
 
 /* ------------------------------------------------------------------ */
 /* Right-hand side b_i = b_I(g, 1_{sigma_i}) = -sum_F nu_{F,t} int_F g dS */
-/* (eq. int_bform with A = Id), Duffy-collapsed 10x10 Gauss per face.   */
+/* (eq. int_bform with A = Id, the problem statement of Sec. 2).        */
+/* A face F of panel i with nu_{F,t} != 0 is a graph tau = P(y) over the  */
+/* panel's spatial triangle K, and nu_{F,t} |F| dS = -+ dA(y) on the     */
+/* lower / upper face, so b_i = int_K g(P_lo(y), y) - g(P_hi(y), y) dA.  */
 /* ------------------------------------------------------------------ */
 
-/* params [nrhs][5] for BEM_DATA_PULSE (NULL for SIN2_UNIFORM); b host
- * [n_tet x nrhs] column-major. */
+/* Built-in data families: params [nrhs][5] for BEM_DATA_PULSE (NULL for
+ * SIN2_UNIFORM); b host [n_tet x nrhs] column-major. Rule per face: K split
+ * into 4^k congruent triangles (k from the data's length scale), each with a
+ * Duffy-collapsed 8 x 8 Gauss-Legendre rule. */
 bem_status bem_rhs(const bem_operator* op, int32_t kind, int32_t nrhs, const double* params, double* b);
+
+/* Quadrature points of the right-hand side for arbitrary Dirichlet data g:
+ * the caller evaluates g at the points and passes the samples to
+ * bem_rhs_from_samples. Points belong to the distinct nu_t != 0 faces of the
+ * mesh ("surfaces", bem_mesh_info's n_surfaces); each face's spatial triangle
+ * K is split into 4^level congruent triangles (level 0..4), each carrying a
+ * Duffy-collapsed n_gauss x n_gauss Gauss-Legendre rule (n_gauss 1..16), so
+ * n_pts = n_surfaces * 4^level * n_gauss^2. pts_txyz [n_pts][4] receives the
+ * space-time points (t, x, y, z) = (P(y), y) and w [n_pts] the weights of
+ * the projected measure dA(y) (their sum over one face is |K|; the sign
+ * -nu_{F,t} is applied per panel by bem_rhs_from_samples). Call with
+ * pts_txyz = w = NULL to get n_pts only. Host arrays. */
+bem_status bem_rhs_points(const bem_operator* op, int32_t level, int32_t n_gauss, int64_t* n_pts, double* pts_txyz,
+                          double* w);
+
+/* b [n_tet x nrhs] (column-major, caller panel order) from samples g
+ * [nrhs][n_pts] of the data at the points of bem_rhs_points with the same
+ * level and n_gauss: per face S_F = sum_q w_q g(x_q) in a fixed order (FP64),
+ * then b_i = S_{F_lo(i)} - S_{F_hi(i)}. Host arrays; computed on the GPU. */
+bem_status bem_rhs_from_samples(const bem_operator* op, int32_t level, int32_t n_gauss, const double* g,
+                                int32_t nrhs, double* b);
 
 /* ------------------------------------------------------------------ */
 /* Matrix-vector products                                               */
 /* ------------------------------------------------------------------ */
 
 /* y_dev = A x_dev for nrhs column-major vectors in FP64 (device pointers),
- * enqueued on `stream` (a cudaStream_t; NULL = context stream). */
+ * enqueued on `stream` (a cudaStream_t; NULL = context stream); returns
+ * without synchronizing. The caller/internal reordering uses a per-operator
+ * workspace, allocated stream-ordered (cudaMallocAsync) on the first call that
+ * needs more room and kept until the operator is destroyed: products of one
+ * operator must not overlap on the GPU (one stream, or ordered streams). */
 bem_status bem_matvec(const bem_operator* op, const double* x_dev, double* y_dev, int32_t nrhs, void* stream);
 
 /* y_dev = A x_dev in the arithmetic `dtype` (BEM_DTYPE_*), same layout as
@@ -213,8 +259,9 @@ bem_status bem_matvec(const bem_operator* op, const double* x_dev, double* y_dev
  * makes a BF16 copy of the values on first use. The products keep packed
  * operands in a per-operator workspace (allocated on first use); the first
  * TF32 / BF16 product of a mesh shape times the candidate launch shapes once
- * and keeps the fastest for the process (so it synchronizes the stream).
- * Synchronizes `stream` before returning. */
+ * and keeps the fastest for the process (so that call synchronizes the
+ * stream). Otherwise stream-ordered like bem_matvec: no allocation once the
+ * workspaces have grown to the call's size, no synchronization. */
 bem_status bem_matvec_dtype(const bem_operator* op, const double* x_dev, double* y_dev, int32_t nrhs,
                             int32_t dtype, void* stream);
 
@@ -267,6 +314,27 @@ bem_status bem_solve(bem_operator* op, const double* b, double* w, int32_t nrhs,
 /* Same on device arrays, enqueued on `stream`; blocks until done. */
 bem_status bem_solve_device(bem_operator* op, const double* b_dev, double* w_dev, int32_t nrhs,
                             const bem_solve_opts* opts, bem_solve_info* info, void* stream);
+
+/* Asynchronous solve: bem_solve_device run by a worker thread of the library
+ * on `stream` (NULL = context stream), returned as a request handle at once.
+ * The GMRES host loop polls a cancellation flag between its blocks of Arnoldi
+ * steps (each block one CUDA-graph launch) and between refinement steps. Until
+ * the request has completed, the caller must not use `op`, b_dev or w_dev. */
+typedef struct bem_request bem_request;
+bem_status bem_solve_async(bem_operator* op, const double* b_dev, double* w_dev, int32_t nrhs,
+                           const bem_solve_opts* opts, void* stream, bem_request** out);
+/* Waits at most timeout_ns (>= 0; 0 polls) for the request. Returns
+ * BEM_ERR_DEVICE_TIMEOUT while it is still running (the request stays valid:
+ * wait again, cancel or destroy it), else the solve's own status, with info
+ * [nrhs] (may be NULL) filled. Never blocks longer than timeout_ns plus
+ * scheduling delay. */
+bem_status bem_request_wait(bem_request* req, int64_t timeout_ns, bem_solve_info* info);
+/* Asks a running solve to stop at its next poll; it then completes with
+ * BEM_ERR_CANCELLED and w_dev holds the iterate reached. */
+bem_status bem_request_cancel(bem_request* req);
+/* Cancels the solve if it is still running, waits for the worker to stop
+ * (at most one block of Arnoldi steps) and frees the request. */
+void bem_request_destroy(bem_request* req);
 
 /* ------------------------------------------------------------------ */
 /* Kernel-level entry: inner integral for arbitrary (point, panel) pairs */

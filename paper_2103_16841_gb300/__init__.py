@@ -17,7 +17,7 @@ import numpy as np
 from . import _lib
 from ._lib import BemError, DATA_PULSE, DATA_SIN2_UNIFORM
 
-__all__ = ["Context", "Mesh", "Operator", "inner_potentials", "BemError", "DATA_PULSE", "DATA_SIN2_UNIFORM"]
+__all__ = ["Context", "Mesh", "Operator", "Request", "inner_potentials", "BemError", "DATA_PULSE", "DATA_SIN2_UNIFORM"]
 
 
 class Context:
@@ -39,6 +39,12 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def alu_peaks(self):
+        """Measured FP32 and FP64 FMA throughput of the device, TFLOP/s."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _lib.check(self._L.bem_alu_peaks(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return {"fp32_tflops": a.value, "fp64_tflops": b.value}
 
     @staticmethod
     def version():
@@ -98,9 +104,10 @@ class Operator:
     """bem_operator: the assembled energetic single-layer Galerkin matrix."""
 
     def __init__(self, ctx: Context, mesh: Mesh, precision: str = "fp64", m_q: int = 3, n_theta: int = 0,
-                 store_fp32: bool = True, matrix_free: bool = False):
+                 store_fp32: bool = True, matrix_free: bool = False, trial_space: str = "p0"):
         self.ctx, self.mesh = ctx, mesh
-        o = _lib.OpOpts(_lib.PREC[precision], int(m_q), int(n_theta), int(bool(store_fp32)), int(bool(matrix_free)))
+        o = _lib.OpOpts(_lib.PREC[precision], int(m_q), int(n_theta), int(bool(store_fp32)), int(bool(matrix_free)),
+                        _lib.TRIAL[trial_space])
         h = ctypes.c_void_p()
         _lib.check(ctx._L.bem_operator_create(ctx.h, mesh.h, ctypes.byref(o), ctypes.byref(h)))
         self.h = h
@@ -168,6 +175,44 @@ class Operator:
         _lib.check(self.ctx._L.bem_rhs(self.h, int(kind), nrhs, pp, _lib.dptr(b)))
         return b.reshape(nrhs, self.n).T.copy()
 
+    def rhs_points(self, level=0, n_gauss=8):
+        """Quadrature points (t, x, y, z) [n_pts, 4] and weights [n_pts] of the
+        right-hand side for arbitrary data (bem_rhs_points)."""
+        n = ctypes.c_int64()
+        _lib.check(self.ctx._L.bem_rhs_points(self.h, int(level), int(n_gauss), ctypes.byref(n), None, None))
+        pts = np.zeros((n.value, 4))
+        w = np.zeros(n.value)
+        _lib.check(self.ctx._L.bem_rhs_points(self.h, int(level), int(n_gauss), ctypes.byref(n), _lib.dptr(pts),
+                                              _lib.dptr(w)))
+        return pts, w
+
+    def rhs_from_samples(self, g, level=0, n_gauss=8):
+        """b [n] or [n, nrhs] from samples g [n_pts] or [n_pts, nrhs] of the data
+        at the points of rhs_points(level, n_gauss)."""
+        g = np.asarray(g, dtype=np.float64)
+        vec = g.ndim == 1
+        G = np.ascontiguousarray((g[:, None] if vec else g).T)
+        nrhs = G.shape[0]
+        b = np.zeros(nrhs * self.n)
+        _lib.check(self.ctx._L.bem_rhs_from_samples(self.h, int(level), int(n_gauss), _lib.dptr(G), nrhs,
+                                                    _lib.dptr(b)))
+        b = b.reshape(nrhs, self.n).T.copy()
+        return b[:, 0] if vec else b
+
+    def solve_async(self, b, w, tol=1e-8, restart=50, maxit=2000, inner="fp64", max_refine=10, stream=None):
+        """Starts bem_solve_async on contiguous CUDA float64 tensors b, w of shape
+        [n] or [nrhs, n]; returns a Request."""
+        import torch
+        for t in (b, w):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ValueError("b and w must be contiguous CUDA float64 tensors")
+        nrhs = 1 if b.dim() == 1 else b.shape[0]
+        o = _lib.SolveOpts(float(tol), int(restart), int(maxit), _lib.DTYPE[inner], int(max_refine))
+        h = ctypes.c_void_p()
+        _lib.check(self.ctx._L.bem_solve_async(self.h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(w.data_ptr()),
+                                               nrhs, ctypes.byref(o), _stream_ptr(stream), ctypes.byref(h)))
+        return Request(self.ctx, h, nrhs)
+
     def matvec(self, x, y=None, stream=None, dtype=None):
         """y = A x for torch CUDA float64 tensors of shape [n] or [nrhs, n].
         dtype None: bem_matvec; "fp64" / "fp32" / "tf32" / "bf16": the
@@ -230,6 +275,38 @@ class Operator:
             pass
 
 
+class Request:
+    """bem_request: an asynchronous solve (Operator.solve_async)."""
+
+    def __init__(self, ctx, handle, nrhs):
+        self.ctx, self.h, self.nrhs = ctx, handle, nrhs
+
+    def wait(self, timeout_s):
+        """bem_request_wait: the solve's status and infos, or None (status
+        BEM_ERR_DEVICE_TIMEOUT) if it is still running after timeout_s."""
+        info = (_lib.SolveInfo * self.nrhs)()
+        st = self.ctx._L.bem_request_wait(self.h, int(max(0.0, timeout_s) * 1e9), info)
+        if st == 5:
+            return None
+        _lib.check(st, allow=(4, 9))
+        return st, [{"iterations": i.iterations, "refinements": i.refinements, "converged": bool(i.converged),
+                     "rel_residual": i.rel_residual, "solve_ms": i.solve_ms} for i in info]
+
+    def cancel(self):
+        _lib.check(self.ctx._L.bem_request_cancel(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx._L.bem_request_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Batch:
     """bem_batch: the operators of many small meshes assembled by one
     persistent launch per pass and solved as one block-diagonal system."""
@@ -237,7 +314,7 @@ class Batch:
     def __init__(self, ctx: Context, meshes, precision="mixed", m_q=3, n_theta=0, store_fp32=True):
         self.ctx = ctx
         self.meshes = list(meshes)          # the meshes must outlive the batch
-        o = _lib.OpOpts(_lib.PREC[precision], int(m_q), int(n_theta), int(bool(store_fp32)), 0)
+        o = _lib.OpOpts(_lib.PREC[precision], int(m_q), int(n_theta), int(bool(store_fp32)), 0, 0)
         arr = (ctypes.c_void_p * len(self.meshes))(*[mm.h.value for mm in self.meshes])
         h = ctypes.c_void_p()
         _lib.check(ctx._L.bem_batch_create(ctx.h, len(self.meshes), arr, ctypes.byref(o), ctypes.byref(h)))
@@ -384,8 +461,13 @@ def inner_potentials(ctx: Context, x4, tets, tet_sv, precision="fp64", n_theta=0
 
 
 def _stream_ptr(stream):
+    """cudaStream_t of `stream`; None gives torch's current stream, so that the
+    library's work is ordered with the torch operations around the call."""
     if stream is None:
-        return None
+        import torch
+        if not torch.cuda.is_available():
+            return None
+        stream = torch.cuda.current_stream()
     if hasattr(stream, "cuda_stream"):
         return ctypes.c_void_p(stream.cuda_stream)
     return ctypes.c_void_p(int(stream))

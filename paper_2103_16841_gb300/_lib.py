@@ -16,19 +16,21 @@ from . import _build
 BEM_OK = 0
 STATUS = {0: "BEM_OK", 1: "BEM_ERR_INVALID_ARG", 2: "BEM_ERR_OUT_OF_MEMORY", 3: "BEM_ERR_CUDA",
           4: "BEM_ERR_NOT_CONVERGED", 5: "BEM_ERR_DEVICE_TIMEOUT", 6: "BEM_ERR_UNSUPPORTED",
-          7: "BEM_ERR_BAD_MESH", 8: "BEM_ERR_INTERNAL"}
+          7: "BEM_ERR_BAD_MESH", 8: "BEM_ERR_INTERNAL", 9: "BEM_ERR_CANCELLED"}
 PREC = {"fp64": 0, "mixed": 1}
+TRIAL = {"p0": 0, "p1": 1}
 DTYPE = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 DATA_SIN2_UNIFORM = 0
 DATA_PULSE = 1
 
 # every symbol include/stbem.h declares
 EXPORTS = [
-    "bem_context_create", "bem_context_destroy", "bem_last_error", "bem_version",
+    "bem_context_create", "bem_context_destroy", "bem_last_error", "bem_version", "bem_alu_peaks",
     "bem_mesh_create", "bem_mesh_create_prisms", "bem_mesh_info", "bem_mesh_destroy",
     "bem_operator_create", "bem_operator_stats", "bem_operator_check", "bem_operator_timings", "bem_operator_reassemble", "bem_operator_export_pattern", "bem_operator_pattern_rows",
     "bem_operator_export_dense", "bem_operator_entries", "bem_operator_destroy",
-    "bem_rhs", "bem_matvec", "bem_matvec_dtype", "bem_matvec_noalloc", "bem_solve", "bem_solve_device", "bem_inner_potentials",
+    "bem_rhs", "bem_rhs_points", "bem_rhs_from_samples", "bem_matvec", "bem_matvec_dtype", "bem_matvec_noalloc", "bem_solve", "bem_solve_device",
+    "bem_solve_async", "bem_request_wait", "bem_request_cancel", "bem_request_destroy", "bem_inner_potentials",
     "bem_batch_create", "bem_batch_stats", "bem_batch_solve", "bem_batch_destroy",
     "bem_server_create", "bem_server_submit", "bem_server_poll", "bem_server_release", "bem_server_stats_get",
     "bem_server_destroy",
@@ -43,7 +45,7 @@ class BemError(RuntimeError):
 
 class OpOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("m_q", ctypes.c_int32), ("n_theta", ctypes.c_int32),
-                ("store_fp32", ctypes.c_int32), ("matrix_free", ctypes.c_int32)]
+                ("store_fp32", ctypes.c_int32), ("matrix_free", ctypes.c_int32), ("trial_space", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -110,6 +112,7 @@ def load(build_if_missing: bool = False):
     L.bem_version.restype = ctypes.c_char_p
     L.bem_context_create.argtypes = [ctypes.c_int, ctypes.POINTER(VP)]
     L.bem_context_destroy.argtypes = [VP]
+    L.bem_alu_peaks.argtypes = [VP, D, D]
     L.bem_context_destroy.restype = None
     L.bem_mesh_create.argtypes = [VP, ctypes.c_int64, D, ctypes.c_int64, I32, D, ctypes.c_int64, I32,
                                   ctypes.POINTER(VP)]
@@ -130,12 +133,19 @@ def load(build_if_missing: bool = False):
     L.bem_operator_destroy.argtypes = [VP]
     L.bem_operator_destroy.restype = None
     L.bem_rhs.argtypes = [VP, ctypes.c_int32, ctypes.c_int32, D, D]
+    L.bem_rhs_points.argtypes = [VP, ctypes.c_int32, ctypes.c_int32, I64, D, D]
+    L.bem_rhs_from_samples.argtypes = [VP, ctypes.c_int32, ctypes.c_int32, D, ctypes.c_int32, D]
     L.bem_matvec.argtypes = [VP, VP, VP, ctypes.c_int32, VP]
     L.bem_matvec_dtype.argtypes = [VP, VP, VP, ctypes.c_int32, ctypes.c_int32, VP]
     L.bem_matvec_noalloc.argtypes = [VP, VP, VP, ctypes.c_int32, VP]
     L.bem_solve.argtypes = [VP, D, D, ctypes.c_int32, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]
     L.bem_solve_device.argtypes = [VP, VP, VP, ctypes.c_int32, ctypes.POINTER(SolveOpts),
                                    ctypes.POINTER(SolveInfo), VP]
+    L.bem_solve_async.argtypes = [VP, VP, VP, ctypes.c_int32, ctypes.POINTER(SolveOpts), VP, ctypes.POINTER(VP)]
+    L.bem_request_wait.argtypes = [VP, ctypes.c_int64, ctypes.POINTER(SolveInfo)]
+    L.bem_request_cancel.argtypes = [VP]
+    L.bem_request_destroy.argtypes = [VP]
+    L.bem_request_destroy.restype = None
     L.bem_inner_potentials.argtypes = [VP, ctypes.c_int64, D, D, I32, ctypes.c_int32, ctypes.c_int32, D]
     L.bem_batch_create.argtypes = [VP, ctypes.c_int32, ctypes.POINTER(VP), ctypes.POINTER(OpOpts), ctypes.POINTER(VP)]
     L.bem_batch_stats.argtypes = [VP, ctypes.POINTER(ctypes.c_int32), I64, I64, D]
@@ -152,7 +162,7 @@ def load(build_if_missing: bool = False):
     L.bem_server_destroy.restype = None
     for name in EXPORTS:
         if name not in ("bem_context_destroy", "bem_mesh_destroy", "bem_operator_destroy", "bem_last_error",
-                        "bem_version", "bem_server_destroy", "bem_batch_destroy"):
+                        "bem_version", "bem_server_destroy", "bem_batch_destroy", "bem_request_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L

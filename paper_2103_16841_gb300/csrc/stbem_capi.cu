@@ -4,12 +4,16 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
 #include <cmath>
 #include <cstring>
 #include <map>
 #include <memory>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "stbem_internal.h"
@@ -405,6 +409,11 @@ bem_status stbem::op_structure_alloc(bem_context* ctx, const bem_mesh* mesh, con
     set_error("unknown precision"); return BEM_ERR_INVALID_ARG;
   }
   if (o.m_q < 1 || o.m_q > 4) { set_error("m_q must be in 1..4"); return BEM_ERR_UNSUPPORTED; }
+  if (o.trial_space == BEM_TRIAL_P1) {
+    set_error("trial space P1 (V_h^1) is not built; only P0 (S_h^0)");
+    return BEM_ERR_UNSUPPORTED;
+  }
+  if (o.trial_space != BEM_TRIAL_P0) { set_error("unknown trial_space"); return BEM_ERR_INVALID_ARG; }
   if (o.n_theta != 0 && (o.n_theta < 4 || o.n_theta > MAX_NTHETA)) {
     set_error("n_theta must be 0 or in 4..32");
     return BEM_ERR_INVALID_ARG;
@@ -490,6 +499,11 @@ bem_status stbem::operator_create(bem_context* ctx, const bem_mesh* mesh, const 
     set_error("unknown precision"); return BEM_ERR_INVALID_ARG;
   }
   if (o.m_q < 1 || o.m_q > 4) { set_error("m_q must be in 1..4"); return BEM_ERR_UNSUPPORTED; }
+  if (o.trial_space == BEM_TRIAL_P1) {
+    set_error("trial space P1 (V_h^1) is not built; only P0 (S_h^0)");
+    return BEM_ERR_UNSUPPORTED;
+  }
+  if (o.trial_space != BEM_TRIAL_P0) { set_error("unknown trial_space"); return BEM_ERR_INVALID_ARG; }
   if (o.n_theta != 0 && (o.n_theta < 4 || o.n_theta > MAX_NTHETA)) {
     set_error("n_theta must be 0 or in 4..32");
     return BEM_ERR_INVALID_ARG;
@@ -555,7 +569,7 @@ void bem_operator_destroy(bem_operator* op) {
   cudaFree(op->d_pts); cudaFree(op->d_pts_trange); cudaFree(op->d_bw); cudaFree(op->d_bnnz);
   cudaFree(op->d_boff); cudaFree(op->d_rsoff); cudaFree(op->d_rs); cudaFree(op->d_val);
   cudaFree(op->d_val32); cudaFree(op->d_tmp); cudaFree(op->d_counter);
-  cudaFree(op->d_val16); cudaFree(op->d_ws);
+  cudaFree(op->d_val16); cudaFree(op->d_ws); cudaFree(op->d_pv);
   delete op;
 }
 
@@ -730,17 +744,85 @@ bem_status bem_rhs(const bem_operator* op, int32_t kind, int32_t nrhs, const dou
   return BEM_OK;
 }
 
+// Room for the two reordered vectors of a product of nn entries each in the
+// operator's workspace; grown stream-ordered on s (the previous block is
+// released on s after the work already enqueued there).
+static bem_status ensure_pv(const bem_operator* op, int64_t nn, cudaStream_t s) {
+  if (op->pv_len >= 2 * nn) return BEM_OK;
+  if (op->d_pv) STBEM_CUDA(cudaFreeAsync(op->d_pv, s));
+  op->d_pv = nullptr;
+  op->pv_len = 0;
+  cudaError_t e = cudaMallocAsync((void**)&op->d_pv, sizeof(double) * 2 * nn, s);
+  if (e != cudaSuccess) {
+    op->d_pv = nullptr;
+    set_error(std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? BEM_ERR_OUT_OF_MEMORY : BEM_ERR_CUDA;
+  }
+  op->pv_len = 2 * nn;
+  return BEM_OK;
+}
+
+static bem_status rhs_rule_args(const bem_operator* op, int32_t level, int32_t n_gauss, int64_t* npps) {
+  if (!op || level < 0 || level > 4 || n_gauss < 1 || n_gauss > 16) {
+    set_error("bem_rhs_points: level must be in 0..4 and n_gauss in 1..16");
+    return BEM_ERR_INVALID_ARG;
+  }
+  *npps = ((int64_t)1 << (2 * level)) * n_gauss * n_gauss;
+  return BEM_OK;
+}
+
+bem_status bem_rhs_points(const bem_operator* op, int32_t level, int32_t n_gauss, int64_t* n_pts, double* pts_txyz,
+                          double* w) {
+  int64_t npps = 0;
+  TRY(rhs_rule_args(op, level, n_gauss, &npps));
+  if (!n_pts) { set_error("bem_rhs_points: n_pts is null"); return BEM_ERR_INVALID_ARG; }
+  const bem_mesh* m = op->mesh;
+  const int64_t n = m->n_surf * npps;
+  *n_pts = n;
+  if (!pts_txyz && !w) return BEM_OK;
+  if (!pts_txyz || !w) { set_error("bem_rhs_points: give both arrays or neither"); return BEM_ERR_INVALID_ARG; }
+  STBEM_CUDA(cudaSetDevice(op->ctx->device));
+  cudaStream_t s = op->ctx->stream;
+  DevBuf<double> dp, dw;
+  TRY(dp.alloc(4 * n)); TRY(dw.alloc(n));
+  TRY(op_rhs_points(op, level, n_gauss, dp.p, dw.p, s));
+  STBEM_CUDA(cudaMemcpyAsync(pts_txyz, dp.p, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, s));
+  STBEM_CUDA(cudaMemcpyAsync(w, dw.p, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  STBEM_CUDA(cudaStreamSynchronize(s));
+  return BEM_OK;
+}
+
+bem_status bem_rhs_from_samples(const bem_operator* op, int32_t level, int32_t n_gauss, const double* g,
+                                int32_t nrhs, double* b) {
+  int64_t npps = 0;
+  TRY(rhs_rule_args(op, level, n_gauss, &npps));
+  if (!g || !b || nrhs <= 0) { set_error("bem_rhs_from_samples: invalid argument"); return BEM_ERR_INVALID_ARG; }
+  const bem_mesh* m = op->mesh;
+  const int64_t n = m->n_surf * npps, nn = m->n_tet * (int64_t)nrhs;
+  STBEM_CUDA(cudaSetDevice(op->ctx->device));
+  cudaStream_t s = op->ctx->stream;
+  DevBuf<double> dw, dg, dS, dbi, db;
+  TRY(dw.alloc(n)); TRY(dg.alloc(n * nrhs)); TRY(dS.alloc(m->n_surf * nrhs)); TRY(dbi.alloc(nn)); TRY(db.alloc(nn));
+  STBEM_CUDA(cudaMemcpyAsync(dg.p, g, sizeof(double) * n * nrhs, cudaMemcpyHostToDevice, s));
+  TRY(op_rhs_points(op, level, n_gauss, nullptr, dw.p, s));
+  TRY(op_rhs_samples(op, level, n_gauss, dw.p, dg.p, nrhs, dS.p, dbi.p, s));
+  TRY(permute(m->d_perm, dbi.p, db.p, m->n_tet, nrhs, false, s));
+  STBEM_CUDA(cudaMemcpyAsync(b, db.p, sizeof(double) * nn, cudaMemcpyDeviceToHost, s));
+  STBEM_CUDA(cudaStreamSynchronize(s));
+  return BEM_OK;
+}
+
 bem_status bem_matvec(const bem_operator* op, const double* x_dev, double* y_dev, int32_t nrhs, void* stream) {
   if (!op || !x_dev || !y_dev || nrhs <= 0) { set_error("bem_matvec: invalid argument"); return BEM_ERR_INVALID_ARG; }
   const bem_mesh* m = op->mesh;
   cudaStream_t s = pick(op->ctx, stream);
   const int64_t nn = m->n_tet * nrhs;
-  DevBuf<double> xi, yi;
-  TRY(xi.alloc(nn)); TRY(yi.alloc(nn));
-  TRY(permute(m->d_perm, x_dev, xi.p, m->n_tet, nrhs, true, s));
-  TRY(op_matvec(op, xi.p, yi.p, nrhs, false, s));
-  TRY(permute(m->d_perm, yi.p, y_dev, m->n_tet, nrhs, false, s));
-  STBEM_CUDA(cudaStreamSynchronize(s));
+  TRY(ensure_pv(op, nn, s));
+  double* xi = op->d_pv;
+  double* yi = op->d_pv + nn;
+  TRY(permute(m->d_perm, x_dev, xi, m->n_tet, nrhs, true, s));
+  TRY(op_matvec(op, xi, yi, nrhs, false, s));
+  TRY(permute(m->d_perm, yi, y_dev, m->n_tet, nrhs, false, s));
   return BEM_OK;
 }
 
@@ -753,12 +835,12 @@ bem_status bem_matvec_dtype(const bem_operator* op, const double* x_dev, double*
   const bem_mesh* m = op->mesh;
   cudaStream_t s = pick(op->ctx, stream);
   const int64_t nn = m->n_tet * nrhs;
-  DevBuf<double> xi, yi;
-  TRY(xi.alloc(nn)); TRY(yi.alloc(nn));
-  TRY(permute(m->d_perm, x_dev, xi.p, m->n_tet, nrhs, true, s));
-  TRY(op_matvec(op, xi.p, yi.p, nrhs, dtype, s));
-  TRY(permute(m->d_perm, yi.p, y_dev, m->n_tet, nrhs, false, s));
-  STBEM_CUDA(cudaStreamSynchronize(s));
+  TRY(ensure_pv(op, nn, s));
+  double* xi = op->d_pv;
+  double* yi = op->d_pv + nn;
+  TRY(permute(m->d_perm, x_dev, xi, m->n_tet, nrhs, true, s));
+  TRY(op_matvec(op, xi, yi, nrhs, dtype, s));
+  TRY(permute(m->d_perm, yi, y_dev, m->n_tet, nrhs, false, s));
   return BEM_OK;
 }
 
@@ -786,7 +868,7 @@ bem_status bem_solve_device(bem_operator* op, const double* b_dev, double* w_dev
   TRY(bi.alloc(nn)); TRY(xi.alloc(nn));
   TRY(permute(m->d_perm, b_dev, bi.p, m->n_tet, nrhs, true, s));
   bem_status st = gmres_solve(op, bi.p, xi.p, nrhs, &o, info, s);
-  if (st != BEM_OK && st != BEM_ERR_NOT_CONVERGED) return st;
+  if (st != BEM_OK && st != BEM_ERR_NOT_CONVERGED && st != BEM_ERR_CANCELLED) return st;
   TRY(permute(m->d_perm, xi.p, w_dev, m->n_tet, nrhs, false, s));
   STBEM_CUDA(cudaStreamSynchronize(s));
   return st;
@@ -805,6 +887,86 @@ bem_status bem_solve(bem_operator* op, const double* b, double* w, int32_t nrhs,
   STBEM_CUDA(cudaMemcpyAsync(w, dw.p, sizeof(double) * nn, cudaMemcpyDeviceToHost, s));
   STBEM_CUDA(cudaStreamSynchronize(s));
   return st;
+}
+
+}  // extern "C"
+
+// An asynchronous solve: bem_solve_device run by a worker thread that polls
+// the request's cancellation flag between blocks of Arnoldi steps.
+struct bem_request {
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool done = false;
+  bem_status status = BEM_OK;
+  std::string error;
+  std::vector<bem_solve_info> info;
+  std::atomic<int> cancel{0};
+};
+
+extern "C" {
+
+bem_status bem_solve_async(bem_operator* op, const double* b_dev, double* w_dev, int32_t nrhs,
+                           const bem_solve_opts* opts, void* stream, bem_request** out) {
+  if (!op || !b_dev || !w_dev || nrhs <= 0 || !out) {
+    set_error("bem_solve_async: invalid argument");
+    return BEM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  std::unique_ptr<bem_request> req(new bem_request());
+  req->info.resize(nrhs);
+  bem_solve_opts o{1e-8, 50, 2000, BEM_DTYPE_FP64, 10};
+  if (opts) o = *opts;
+  bem_request* r = req.get();
+  const int dev = op->ctx->device;
+  try {
+    r->worker = std::thread([r, op, b_dev, w_dev, nrhs, o, stream, dev]() {
+      bem_status st = BEM_OK;
+      if (cudaSetDevice(dev) != cudaSuccess) {
+        set_error("cudaSetDevice failed in the solve worker");
+        st = BEM_ERR_CUDA;
+      } else {
+        set_thread_cancel_flag(&r->cancel);
+        st = bem_solve_device(op, b_dev, w_dev, nrhs, &o, r->info.data(), stream);
+        set_thread_cancel_flag(nullptr);
+      }
+      std::lock_guard<std::mutex> lk(r->mu);
+      r->status = st;
+      r->error = st == BEM_OK ? std::string() : std::string(bem_last_error());
+      r->done = true;
+      r->cv.notify_all();
+    });
+  } catch (...) {
+    set_error("bem_solve_async: could not start the worker thread");
+    return BEM_ERR_INTERNAL;
+  }
+  *out = req.release();
+  return BEM_OK;
+}
+
+bem_status bem_request_wait(bem_request* req, int64_t timeout_ns, bem_solve_info* info) {
+  if (!req || timeout_ns < 0) { set_error("bem_request_wait: invalid argument"); return BEM_ERR_INVALID_ARG; }
+  std::unique_lock<std::mutex> lk(req->mu);
+  if (!req->cv.wait_for(lk, std::chrono::nanoseconds(timeout_ns), [req] { return req->done; })) {
+    set_error("bem_request_wait: the solve is still running");
+    return BEM_ERR_DEVICE_TIMEOUT;
+  }
+  if (info) std::copy(req->info.begin(), req->info.end(), info);
+  if (req->status != BEM_OK) set_error(req->error);
+  return req->status;
+}
+
+bem_status bem_request_cancel(bem_request* req) {
+  if (!req) { set_error("bem_request_cancel: null request"); return BEM_ERR_INVALID_ARG; }
+  req->cancel.store(1);
+  return BEM_OK;
+}
+
+void bem_request_destroy(bem_request* req) {
+  if (!req) return;
+  req->cancel.store(1);
+  if (req->worker.joinable()) req->worker.join();
+  delete req;
 }
 
 bem_status bem_inner_potentials(bem_context* ctx, int64_t n, const double* x4, const double* tets,

@@ -585,15 +585,19 @@ __device__ __forceinline__ void quad_block(const BlockCtx& B, int64_t b, unsigne
           const int k = base + lane;
           int na = 0, q = 0, s = 0;
           float et = 0.f;
+          bool need64 = false;
           if (k < ncut) {
             const int it = mycut[k];
             q = it / nsw;
             s = it - q * nsw;
             float Fv[3], cc = 0.f;
             face_class_mixed(mypc[q], Ff[slo + s], Fv, cc, fdiam);
-            FaceCutIn<float> in;
-            cut_in_mixed(mypc[q], Ff[slo + s], Fv, cc, Fs[slo + s], in);
-            et = (float)face_cut<float>(CR, mypc[q], in, B.rule, myarc + 3 * lane, &na);
+            need64 = near_singular_mixed(cc, mypc[q].F.d, fdiam);
+            if (!need64) {
+              FaceCutIn<float> in;
+              cut_in_mixed(mypc[q], Ff[slo + s], Fv, cc, Fs[slo + s], in);
+              et = (float)face_cut<float>(CR, mypc[q], in, B.rule, myarc + 3 * lane, &na);
+            }
           }
           int incl = na;
 #pragma unroll
@@ -612,7 +616,7 @@ __device__ __forceinline__ void quad_block(const BlockCtx& B, int64_t b, unsigne
           if (k < ncut) {
             float v = et;
             for (int i = 0; i < na; ++i) v += myval[3 * lane + i];
-            if (!isfinite(v))   // degenerate FP32 geometry: this face in FP64
+            if (need64 || !isfinite(v))   // near-singular or degenerate FP32 geometry: this face in FP64
               v = (float)face_W_fp64(P + 4 * q, C.G, Fs[slo + s], B.n_theta);
             Wsc[q * B.max_surf + s] = v;
           }
@@ -1200,6 +1204,104 @@ bem_status op_rhs(const bem_operator* op, int kind, int nrhs, const double* d_pa
   const bem_mesh* m = op->mesh;
   k_rhs<<<(unsigned)((m->n_tet + 127) / 128), 128, 0, s>>>(m->n_tet, m->d_tet, m->d_surf, m->d_col, kind, nrhs,
                                                            d_params, d_b);
+  STBEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+// Points and weights of the right-hand side rule for arbitrary data: per
+// surface (a face tau = P(y) over K), K split into 4^level congruent
+// triangles in the order of k_rhs (row p, then q; upright, then inverted),
+// each with a Duffy-collapsed ng x ng Gauss-Legendre rule. One thread per
+// (surface, sub-triangle); pts may be null (weights only).
+__global__ void k_rhs_points(int64_t n_surf, const SurfDev* surf, const ColGeom* cols, int level, int ng,
+                             double* pts, double* wts) {
+  const int m = 1 << level, nsub = m * m;
+  int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= n_surf * nsub) return;
+  const int64_t sidx = tid / nsub;
+  const int k = (int)(tid - sidx * nsub);
+  // sub-triangle k -> corners (barycentric)
+  double a0[3], a1[3], a2[3];
+  int cnt = 0;
+  bool found = false;
+  for (int p = 0; p < m && !found; ++p)
+    for (int q = 0; p + q < m && !found; ++q) {
+      double u0[3] = {1.0 - (double)(p + q) / m, (double)p / m, (double)q / m};
+      double u1[3] = {1.0 - (double)(p + q + 1) / m, (double)(p + 1) / m, (double)q / m};
+      double u2[3] = {1.0 - (double)(p + q + 1) / m, (double)p / m, (double)(q + 1) / m};
+      if (cnt++ == k) {
+        for (int c = 0; c < 3; ++c) { a0[c] = u0[c]; a1[c] = u1[c]; a2[c] = u2[c]; }
+        found = true;
+      } else if (p + q + 2 <= m) {
+        if (cnt++ == k) {
+          double v0[3] = {1.0 - (double)(p + q + 2) / m, (double)(p + 1) / m, (double)(q + 1) / m};
+          for (int c = 0; c < 3; ++c) { a0[c] = u1[c]; a1[c] = v0[c]; a2[c] = u2[c]; }
+          found = true;
+        }
+      }
+    }
+  const SurfDev S = surf[sidx];
+  const ColGeom& G = cols[S.col];
+  const double* X = gl_x() + ng * (ng - 1) / 2;
+  const double* Wt = gl_w() + ng * (ng - 1) / 2;
+  const double jac = 2.0 * G.area / (double)nsub;   // Duffy: 2 |sub| u
+  int64_t o = (sidx * nsub + k) * (int64_t)ng * ng;
+  for (int a = 0; a < ng; ++a) {
+    const double u = 0.5 * (X[a] + 1.0), wu = 0.5 * Wt[a];
+    for (int c = 0; c < ng; ++c, ++o) {
+      const double v = 0.5 * (X[c] + 1.0), wv = 0.5 * Wt[c];
+      const double m0 = 1.0 - u, m1 = u * (1.0 - v), m2 = u * v;
+      double l[3];
+      for (int e = 0; e < 3; ++e) l[e] = m0 * a0[e] + m1 * a1[e] + m2 * a2[e];
+      wts[o] = jac * wu * wv * u;
+      if (pts) {
+        pts[4 * o] = l[0] * S.f.p[0] + l[1] * S.f.p[1] + l[2] * S.f.p[2];
+        for (int e = 0; e < 3; ++e) pts[4 * o + 1 + e] = l[0] * G.X[0][e] + l[1] * G.X[1][e] + l[2] * G.X[2][e];
+      }
+    }
+  }
+}
+
+// S[r][s] = sum_q w_q g[r][s * npps + q] in ascending q (one thread per (r, s))
+__global__ void k_rhs_face_sums(int64_t n_surf, int64_t npps, int nrhs, const double* wts, const double* g,
+                                double* S) {
+  int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= n_surf * nrhs) return;
+  const int64_t r = tid / n_surf, sidx = tid - r * n_surf;
+  const double* gw = g + r * n_surf * npps + sidx * npps;
+  const double* ww = wts + sidx * npps;
+  double acc = 0.0;
+  for (int64_t q = 0; q < npps; ++q) acc += ww[q] * gw[q];
+  S[tid] = acc;
+}
+
+// b[r][i] = S[r][lo(i)] - S[r][hi(i)] (internal panel order)
+__global__ void k_rhs_combine(int64_t n_tet, int64_t n_surf, int nrhs, const TetDev* tets, const double* S, double* b) {
+  int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= n_tet * nrhs) return;
+  const int64_t r = tid / n_tet, i = tid - r * n_tet;
+  const TetDev& D = tets[i];
+  b[tid] = S[r * n_surf + D.lo] - S[r * n_surf + D.hi];
+}
+
+bem_status op_rhs_points(const bem_operator* op, int level, int ng, double* d_pts, double* d_wts, cudaStream_t s) {
+  const bem_mesh* m = op->mesh;
+  const int64_t n = m->n_surf * ((int64_t)1 << (2 * level));
+  if (n == 0) return BEM_OK;
+  k_rhs_points<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(m->n_surf, m->d_surf, m->d_col, level, ng, d_pts, d_wts);
+  STBEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+bem_status op_rhs_samples(const bem_operator* op, int level, int ng, const double* d_wts, const double* d_g, int nrhs,
+                          double* d_S, double* d_b, cudaStream_t s) {
+  const bem_mesh* m = op->mesh;
+  const int64_t npps = ((int64_t)1 << (2 * level)) * ng * ng;
+  const int64_t ns = m->n_surf * nrhs, nb = m->n_tet * nrhs;
+  if (ns > 0)
+    k_rhs_face_sums<<<(unsigned)((ns + 127) / 128), 128, 0, s>>>(m->n_surf, npps, nrhs, d_wts, d_g, d_S);
+  if (nb > 0)
+    k_rhs_combine<<<(unsigned)((nb + 127) / 128), 128, 0, s>>>(m->n_tet, m->n_surf, nrhs, m->d_tet, d_S, d_b);
   STBEM_CUDA(cudaGetLastError());
   return BEM_OK;
 }

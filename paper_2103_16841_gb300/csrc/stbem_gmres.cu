@@ -231,12 +231,17 @@ __global__ void k_residual(const double* __restrict__ b, const double* __restric
 
 unsigned grid_of(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)); }
 
+// GMRES workspace, allocated and released stream-ordered on the solve's
+// stream (no device-wide synchronization when it is freed, so the solves of
+// concurrent requests on other streams keep running)
 template <typename T>
 struct DA {
   T* p = nullptr;
-  ~DA() { if (p) cudaFree(p); }
+  cudaStream_t st = nullptr;
+  ~DA() { if (p) cudaFreeAsync(p, st); }
   bem_status alloc(int64_t n, bool zero, cudaStream_t s) {
-    if (cudaMalloc((void**)&p, sizeof(T) * std::max<int64_t>(n, 1)) != cudaSuccess) {
+    st = s;
+    if (cudaMallocAsync((void**)&p, sizeof(T) * std::max<int64_t>(n, 1), s) != cudaSuccess) {
       cudaGetLastError();
       p = nullptr;
       set_error("out of device memory (GMRES workspace)");
@@ -391,6 +396,10 @@ bem_status gmres_device(const SegLayout& L, const MatvecFn& mv, const double* d_
   // steps per graph launch; the graph is captured on the first use
   const int q = std::min(m, 8);
   cudaGraphExec_t gexec = nullptr;
+  struct ExecGuard {
+    cudaGraphExec_t* g;
+    ~ExecGuard() { if (*g) cudaGraphExecDestroy(*g); *g = nullptr; }
+  } exec_guard{&gexec};
   bool graph_ok = true;
   int total = 0;
   int nact = 0;
@@ -407,6 +416,7 @@ bem_status gmres_device(const SegLayout& L, const MatvecFn& mv, const double* d_
     STBEM_CUDA(cudaMemcpyAsync(&nact, G.nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
     STBEM_CUDA(cudaStreamSynchronize(s));
     if (nact == 0) break;
+    if (cancel_requested()) { set_error("solve cancelled"); return BEM_ERR_CANCELLED; }
     int j = 0;
     while (j < m && total < maxit && nact > 0) {
       const int nb = std::min(q, m - j);
@@ -441,13 +451,18 @@ bem_status gmres_device(const SegLayout& L, const MatvecFn& mv, const double* d_
       total += nb;
       STBEM_CUDA(cudaMemcpyAsync(&nact, G.nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
       STBEM_CUDA(cudaStreamSynchronize(s));
+      if (cancel_requested()) break;   // x += V y below keeps the iterate reached
     }
     // x += V y
     k_backsolve<<<gC, 64, 0, s>>>(G, C, m);
     k_combine<<<gN, 256, 0, s>>>(V.p, NN, y.p, m, nullptr, m, 1.0, d_x, N, K, S, d_seg);
     STBEM_CUDA(cudaGetLastError());
+    if (cancel_requested()) {
+      STBEM_CUDA(cudaStreamSynchronize(s));
+      set_error("solve cancelled");
+      return BEM_ERR_CANCELLED;
+    }
   }
-  if (gexec) cudaGraphExecDestroy(gexec);
   // true residuals
   G_TRY(mv(d_x, w.p, s));
   k_residual<<<gN, 256, 0, s>>>(d_b, w.p, r.p, NN);

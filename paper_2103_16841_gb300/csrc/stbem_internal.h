@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <functional>
 #include <memory>
 #include <string>
@@ -96,6 +97,8 @@ struct bem_operator {
   mutable uint16_t* d_val16 = nullptr;  // BF16 copy of the values
   mutable float* d_ws = nullptr;        // packed operands of the FP32 / tensor-core products
   mutable int64_t ws_len = 0;
+  mutable double* d_pv = nullptr;       // caller-order <-> internal-order vectors of the products
+  mutable int64_t pv_len = 0;           // (stream-ordered allocation, grown on demand)
   // optional admission hook, called once the sparsity structure is known
   // (nstored, nrows_stored, tmp_len set) and before the value arrays are allocated
   std::function<bem_status(const bem_operator*)> admit;
@@ -143,6 +146,11 @@ struct BatchMatvec {
   bem_status apply(const double* x, double* y, int K, int arith, cudaStream_t s);
   ~BatchMatvec();
 };
+// Cancellation of a solve run by a worker thread (bem_solve_async): the
+// thread installs its request's flag; the GMRES host loops poll it between
+// blocks of Arnoldi steps and return BEM_ERR_CANCELLED once it is set.
+void set_thread_cancel_flag(const std::atomic<int>* flag);
+bool cancel_requested();
 // per-column 2-norms of a [K][N] vector (host result)
 bem_status seg_norms(const SegLayout& L, const double* v, std::vector<double>& out, cudaStream_t s);
 // refined solve over a layout: FP64 GMRES with mv_hi, or inner GMRES with
@@ -180,6 +188,11 @@ int64_t operator_value_bytes(const bem_operator* op);
 enum { MV_FP64 = 0, MV_FP32 = 1, MV_TF32 = 2, MV_BF16 = 3 };
 bem_status op_matvec(const bem_operator* op, const double* x, double* y, int nrhs, int arith, cudaStream_t s);
 bem_status op_rhs(const bem_operator* op, int kind, int nrhs, const double* d_params, double* d_b, cudaStream_t s);
+// right-hand side rule for arbitrary data (points [n_surf * 4^level * ng^2][4], weights)
+bem_status op_rhs_points(const bem_operator* op, int level, int ng, double* d_pts, double* d_wts, cudaStream_t s);
+// b (internal order, [nrhs][n_tet]) from samples g [nrhs][n_pts]; d_S scratch [nrhs][n_surf]
+bem_status op_rhs_samples(const bem_operator* op, int level, int ng, const double* d_wts, const double* d_g, int nrhs,
+                          double* d_S, double* d_b, cudaStream_t s);
 bem_status op_value_scan(const bem_operator* op, int64_t* nbad, double* maxabs, cudaStream_t s);
 bem_status op_entries(const bem_operator* op, int64_t n, const int32_t* d_ij, double* d_out, cudaStream_t s);
 bem_status op_pattern_csr(const bem_operator* op, int64_t* d_rowcount, int64_t* d_rowptr, int32_t* d_cols,

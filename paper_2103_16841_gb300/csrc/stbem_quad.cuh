@@ -90,7 +90,12 @@ struct PtR {             // apex-against-column quantities in precision R (colum
   R ps[3];               // signed distance of xb to edge line k (> 0 inside)
   R ws[3];               // coordinate of Q[k] along edge k, origin at the foot of xb
   R rs[3];               // |x_s - corner_k| in precision R
-  R Efull[3];            // int (r - |d|) dphi along the whole edge k
+  R Efull[3];            // int (r - |d|) dphi along the whole edge k (far field: int (r - C) dphi)
+  // far field of the mixed path (see edge_far): the contour integrand is
+  // r - C with C = |x_s - corner 0|; far_rho: lower bound of the in-plane
+  // distance from xb to K
+  int far;
+  R C, far_rho;
 };
 
 struct PointCol {        // apex x against one column
@@ -246,6 +251,115 @@ STBEM_HD inline R edge_int(R wa, R dw, R p_s, R d, const ArcRule& rule) {
   return edge_dE<R>(wa, dw, p_s, d);
 }
 
+// ---------------------------------------------------------------------------
+// Far field of the mixed path. When the foot point xb lies far outside K
+// (in-plane distance rho_K >= FAR_RHO diam K), every piece of
+// oint (r - |d|) dphi is O(diam K) while their sum, 4 pi W, is
+// O(diam K^2 / dist): the FP32 terms would keep only eps rho_K / diam K of
+// relative accuracy. Since xb then lies outside the lit set R, oint C dphi = 0
+// around dR for any constant C, so
+//     4 pi W = oint_{dR} (r - C) dphi,   C = |x_s - corner 0|,
+// and with u the point in column coordinates (origin at corner 0) and
+// q0 = corner 0 - xb,
+//     r - C = (|q|^2 - |q0|^2) / (r + C) = <u, 2 q0 + u> / (r + C),
+// formed from O(diam K) coordinates, so every piece is O(diam K^2 / dist)
+// with relative accuracy eps. Edge pieces are integrated in the edge
+// parameter, conic arcs over their chord (arc_far); both rules are
+// Gauss-Legendre with the order taken from the nearest complex zero of |q|^2.
+// ---------------------------------------------------------------------------
+constexpr float FAR_RHO = 1.5f;
+
+// Gauss-Legendre order reaching relative accuracy tol on [-1, 1] for an
+// integrand analytic except at z = a +- i b (Bernstein ellipse parameter)
+template <typename R>
+STBEM_HD inline int gauss_order(R a, R b, double tol, int nmin, int nmax) {
+  const R s = R(0.5) * (sqrt((a - R(1)) * (a - R(1)) + b * b) + sqrt((a + R(1)) * (a + R(1)) + b * b));
+  const R rho = s + sqrt(fmax(s * s - R(1), R(0)));
+  if (!(rho > R(1.0001))) return nmax;
+  const int n = (int)ceil(log((R)(1.0 / tol)) / (R(2) * log(rho))) + 1;
+  return n < nmin ? nmin : (n > nmax ? nmax : n);
+}
+
+// int (r - C) dphi along edge k for u = Q_k + lambda L_k U_k, lambda in
+// [la, lb]: dphi = p_s L_k dlambda / |q|^2 (p_s the signed distance of xb to
+// the edge line, constant along it)
+template <typename R>
+STBEM_HD inline R edge_far(const PtR<R>& P, const ColR<R>& G, int k, R la, R lb, const ArcRule& rule) {
+  const R h = R(0.5) * (lb - la);
+  if (!(h > R(0))) return R(0);
+  const R mid = R(0.5) * (la + lb), L = G.L[k];
+  const R q0x = -P.xb[0], q0y = -P.xb[1];
+  // |q|^2 = 0 at lambda = lambda_foot +- i |p_s| / L
+  const int n = gauss_order<R>((-P.ws[k] / L - mid) / h, fabs(P.ps[k]) / (L * h), rule.tol, 3, 10);
+  const double* X = gl_x() + n * (n - 1) / 2;
+  const double* Wt = gl_w() + n * (n - 1) / 2;
+  const R ex = G.U[k][0] * L, ey = G.U[k][1] * L, d2 = P.d * P.d;
+  R acc = R(0);
+  for (int i = 0; i < n; ++i) {
+    const R lam = mid + h * (R)X[i];
+    const R ux = G.Q[k][0] + lam * ex, uy = G.Q[k][1] + lam * ey;
+    const R qx = q0x + ux, qy = q0y + uy, q2 = qx * qx + qy * qy;
+    const R r = sqrt(q2 + d2);
+    const R del = (ux * (R(2) * q0x + ux) + uy * (R(2) * q0y + uy)) / (r + P.C);
+    acc += (R)Wt[i] * del / q2;
+  }
+  return acc * P.ps[k] * L * h;
+}
+
+// int (r - C) dphi along the conic dE from event uA to event uB (column
+// coordinates), E on the left. With u = y - uA the conic is
+//     2 <m, u> + Q(u) = 0,   m = q_A + r_A g,   Q(u) = |u|^2 - <g, u>^2,
+// (square of |x - y| = r_A - <g, u>, which holds on the cone since
+// tau = P(y) is linear). Over the chord, u = s D + h(s) nu (D = uB - uA, nu
+// its left unit normal): a h^2 + b(s) h + c(s) = 0 with a = Q(nu),
+// b = 2 <m, nu> + 2 s B(D, nu), c = s (s - 1) Q(D) (B on the conic), h the
+// small root (h(0) = h(1) = 0). On the arc r - C = (r_A - C) - <g, u>. Applies
+// to arcs that are nearly straight with E on the left (b < 0 on [0, 1],
+// sagitta <= |D| / 16); returns false otherwise (the caller takes conic_arc).
+template <typename R>
+STBEM_HD inline bool arc_far(const R* xb, R d, R C, R far_rho, const R* g, const R* uA, const R* D, const ArcRule& rule,
+                             R& out) {
+  const R Dx = D[0], Dy = D[1];
+  const R l2 = Dx * Dx + Dy * Dy;
+  if (!(l2 > R(0))) { out = R(0); return true; }
+  const R l = sqrt(l2), nx = -Dy / l, ny = Dx / l;
+  const R q0x = -xb[0], q0y = -xb[1];
+  const R qAx = q0x + uA[0], qAy = q0y + uA[1];
+  const R rA = sqrt(qAx * qAx + qAy * qAy + d * d);
+  const R mx = qAx + rA * g[0], my = qAy + rA * g[1];
+  const R gD = g[0] * Dx + g[1] * Dy, gn = g[0] * nx + g[1] * ny;
+  const R QD = l2 - gD * gD, a = R(1) - gn * gn, BDn = -gD * gn;
+  const R b0 = R(2) * (mx * nx + my * ny), b1 = b0 + R(2) * BDn;
+  if (!(b0 < R(0) && b1 < R(0))) return false;
+  {
+    const R bh = R(0.5) * (b0 + b1), ch = R(-0.25) * QD;
+    const R disc = bh * bh - R(4) * a * ch;
+    if (!(disc > R(0))) return false;
+    const R hh = R(-2) * ch / (bh - sqrt(disc));
+    if (!(fabs(hh) <= R(0.0625) * l)) return false;
+  }
+  const R delA = (uA[0] * (R(2) * q0x + uA[0]) + uA[1] * (R(2) * q0y + uA[1])) / (rA + C);
+  // |q|^2 has no zero within far_rho of the chord (it lies in K)
+  const int n = gauss_order<R>(R(0), R(2) * far_rho / l, rule.tol, 4, 10);
+  const double* X = gl_x() + n * (n - 1) / 2;
+  const double* Wt = gl_w() + n * (n - 1) / 2;
+  R acc = R(0);
+  for (int i = 0; i < n; ++i) {
+    const R sv = R(0.5) * (R(1) + (R)X[i]);
+    const R c = sv * (sv - R(1)) * QD, b = b0 + R(2) * sv * BDn;
+    const R disc = fmax(b * b - R(4) * a * c, R(0));
+    const R h = R(-2) * c / (b - sqrt(disc));
+    const R dh = -((R(2) * sv - R(1)) * QD + R(2) * BDn * h) / (R(2) * a * h + b);
+    const R wx = sv * Dx + h * nx, wy = sv * Dy + h * ny;   // u - uA
+    const R tx = Dx + dh * nx, ty = Dy + dh * ny;
+    const R qx = qAx + wx, qy = qAy + wy, q2 = qx * qx + qy * qy;
+    const R del = delA - (g[0] * wx + g[1] * wy);
+    acc += (R)Wt[i] * del * (qx * ty - qy * tx) / q2;
+  }
+  out = R(0.5) * acc;
+  return true;
+}
+
 // Geometry of apex x against column G and the whole-triangle potential (the
 // fully lit case). FP64 path: everything in FP64. Mixed path: the relative
 // position, the height d, the foot point and the corner distances in FP64
@@ -280,9 +394,26 @@ STBEM_HD inline void point_col(const double* x, const ColGeom& G, PointCol& P, b
       T.ws[k] = T.q[k][0] * ux + T.q[k][1] * uy;
       if (!(T.ps[k] > 0.f)) in = 0;
       out = fmaxf(out, -T.ps[k]);
-      T.Efull[k] = edge_int<float>(T.ws[k], (float)G.L[k], T.ps[k], T.d, er);
-      W += T.Efull[k];
       split2(P.r[k] - P.t, P.rho_hi[k], P.rho_lo[k]);
+    }
+    T.far = out >= FAR_RHO * (float)G.diam;
+    T.C = T.rs[0];
+    T.far_rho = out;
+    if (T.far) {
+      ColR<float> CR;
+      for (int k = 0; k < 3; ++k) {
+        CR.Q[k][0] = (float)G.Q[k][0]; CR.Q[k][1] = (float)G.Q[k][1];
+        CR.U[k][0] = (float)G.U[k][0]; CR.U[k][1] = (float)G.U[k][1]; CR.L[k] = (float)G.L[k];
+      }
+      for (int k = 0; k < 3; ++k) {
+        T.Efull[k] = edge_far<float>(T, CR, k, 0.f, 1.f, er);
+        W += T.Efull[k];
+      }
+    } else {
+      for (int k = 0; k < 3; ++k) {
+        T.Efull[k] = edge_int<float>(T.ws[k], (float)G.L[k], T.ps[k], T.d, er);
+        W += T.Efull[k];
+      }
     }
     P.inK = in;
     P.rlo = sqrt(d * d + (double)out * (double)out);
@@ -296,6 +427,9 @@ STBEM_HD inline void point_col(const double* x, const ColGeom& G, PointCol& P, b
     return;
   }
   PtR<double>& D = P.D;
+  D.far = 0;
+  D.C = 0.0;
+  D.far_rho = 0.0;
   D.d = d;
   D.xb[0] = xb0;
   D.xb[1] = xb1;
@@ -716,6 +850,14 @@ STBEM_HD inline int face_class_mixed(const PointCol& P, const FaceF& Fc, float* 
   return FACE_CUT;
 }
 
+// Near-singular faces of the mixed path: the apex lies nearly in the plane
+// of K and the cone's vertex nearly on it (|c|, |d| < 0.03 diam K), so the
+// conic passes close to the foot point, where FP32 arcs lose accuracy; the
+// mixed path computes these faces in FP64.
+STBEM_HD inline bool near_singular_mixed(float c, float d, float diam) {
+  return fmaxf(fabsf(c), fabsf(d)) < 0.03f * diam;
+}
+
 // Inputs of the cut case in precision R: cone-function values F_k at the
 // corners, a0_k = t - p_k, a1_k = p_{k+1} - p_k, the in-frame gradient g,
 // c = t - P(xb); c64 / g64 feed the FP64 closed form of coplanar (d = 0) arcs.
@@ -754,14 +896,36 @@ STBEM_HD inline void cut_in_mixed(const PointCol& P, const FaceF& Fc, const floa
 // A conic arc of a cut face (d != 0) recorded for evaluation later: the
 // quadrature kernel collects the arcs of all cut pairs of a warp and then
 // integrates them one per lane over the compacted list.
+// Far-field arcs (far != 0) keep A in column coordinates and the apex data
+// of the far-field form (foot point xb, C, far_rho).
 template <typename R>
 struct ArcRec {
   R A[2], dAB[2], c, d, g[2];
-  int full, tiny_is_short;
+  R xb[2], C, far_rho;
+  int full, tiny_is_short, far, pad;
 };
+
+// A far-field arc over its chord (arc_far), or conic_arc shifted from the
+// integrand r - |d| to r - C by (|d| - C) times the angle the arc spans at xb
+// (strongly curved arcs, or the long way round). A: start in column
+// coordinates.
+template <typename R>
+STBEM_HD inline R far_arc_value(const R* xb, R d, R C, R far_rho, R c, const R* g, const R* A, const R* dAB,
+                                bool tiny_short, const ArcRule& rule, double c64, const double* g64) {
+  R v;
+  if (arc_far<R>(xb, d, C, far_rho, g, A, dAB, rule, v)) return v;
+  const R ya[2] = {A[0] - xb[0], A[1] - xb[1]};
+  v = conic_arc<R>(ya, dAB, false, c, d, g, rule, c64, g64, tiny_short);
+  const R bx = ya[0] + dAB[0], by = ya[1] + dAB[1];
+  const R dphi = atan2(ya[0] * by - ya[1] * bx, ya[0] * bx + ya[1] * by);
+  return v - (xb[0] * xb[0] + xb[1] * xb[1]) / (C + fabs(d)) * dphi;
+}
 
 template <typename R>
 STBEM_HD inline R arc_value(const ArcRec<R>& a, const ArcRule& rule) {
+  if (a.far)
+    return far_arc_value<R>(a.xb, a.d, a.C, a.far_rho, a.c, a.g, a.A, a.dAB, a.tiny_is_short != 0, rule, 0.0,
+                            nullptr);
   return conic_arc<R>(a.full ? nullptr : a.A, a.full ? nullptr : a.dAB, a.full != 0, a.c, a.d, a.g, rule, 0.0,
                       nullptr, a.tiny_is_short != 0);
 }
@@ -825,6 +989,7 @@ STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, con
     }
     if (!has) continue;
     if (!la_root && !lb_root) total += P.Efull[k];
+    else if (P.far) total += edge_far<R>(P, G, k, la, lb, rule);
     else total += edge_int<R>(P.ws[k] + la * G.L[k], (lb - la) * G.L[k], P.ps[k], d, rule);
     // events relative to xb (O(distance)) and in column coordinates (O(diam K));
     // differences of the latter give arc spans without cancellation
@@ -850,9 +1015,21 @@ STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, con
         int j = (i + s) % nev;
         if (ev_in[j]) {
           R dAB[2] = {ev_l[j][0] - ev_l[i][0], ev_l[j][1] - ev_l[i][1]};
+          if (P.far && !(defer && d != R(0))) {
+            total += far_arc_value<R>(P.xb, d, P.C, P.far_rho, c, g, ev_l[i], dAB, tiny_short, rule, in.c64,
+                                      in.g64);
+            break;
+          }
           if (defer && d != R(0)) {
             ArcRec<R>& a = defer[(*ndefer)++];
-            a.A[0] = ev_y[i][0]; a.A[1] = ev_y[i][1]; a.dAB[0] = dAB[0]; a.dAB[1] = dAB[1];
+            a.far = P.far;
+            if (P.far) {
+              a.A[0] = ev_l[i][0]; a.A[1] = ev_l[i][1];
+              a.xb[0] = P.xb[0]; a.xb[1] = P.xb[1]; a.C = P.C; a.far_rho = P.far_rho;
+            } else {
+              a.A[0] = ev_y[i][0]; a.A[1] = ev_y[i][1];
+            }
+            a.dAB[0] = dAB[0]; a.dAB[1] = dAB[1];
             a.c = c; a.d = d; a.g[0] = g[0]; a.g[1] = g[1]; a.full = 0; a.tiny_is_short = tiny_short;
           } else {
             total += conic_arc<R>(ev_y[i], dAB, false, c, d, g, rule, in.c64, in.g64, tiny_short);
@@ -875,7 +1052,7 @@ STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, con
     if (defer && d != R(0)) {
       ArcRec<R>& a = defer[(*ndefer)++];
       a.A[0] = a.A[1] = a.dAB[0] = a.dAB[1] = R(0);
-      a.c = c; a.d = d; a.g[0] = g[0]; a.g[1] = g[1]; a.full = 1; a.tiny_is_short = 0;
+      a.c = c; a.d = d; a.g[0] = g[0]; a.g[1] = g[1]; a.full = 1; a.tiny_is_short = 0; a.far = 0;
     } else {
       total += conic_arc<R>(nullptr, nullptr, true, c, d, g, rule, in.c64, in.g64);
     }
@@ -902,6 +1079,7 @@ STBEM_HD inline double face_W(const ColGeom& G, const PointCol& P, const FaceGeo
     int cls = face_class_mixed(P, Ff, F, c, (float)G.diam);
     if (cls == FACE_LIT) return P.Wst;
     if (cls == FACE_DARK) return 0.0;
+    if (near_singular_mixed(c, P.F.d, (float)G.diam)) return nan("");   // the caller recomputes it in FP64
     ColR<float> CR;
     make_colr<float>(G, CR);
     FaceCutIn<float> in;

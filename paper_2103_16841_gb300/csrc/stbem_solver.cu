@@ -14,6 +14,13 @@
 namespace stbem {
 
 namespace {
+thread_local const std::atomic<int>* t_cancel = nullptr;
+}  // namespace
+
+void set_thread_cancel_flag(const std::atomic<int>* flag) { t_cancel = flag; }
+bool cancel_requested() { return t_cancel && t_cancel->load(std::memory_order_relaxed) != 0; }
+
+namespace {
 
 __global__ void k_sub(const double* a, const double* b, double* out, int64_t n) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -25,9 +32,15 @@ __global__ void k_axpy(double alpha, const double* x, double* y, int64_t n) {
   if (idx < n) y[idx] += alpha * x[idx];
 }
 
+// refinement vectors, stream-ordered like the GMRES workspace
 struct Dev {
   double* p = nullptr;
-  ~Dev() { if (p) cudaFree(p); }
+  cudaStream_t st = nullptr;
+  ~Dev() { if (p) cudaFreeAsync(p, st); }
+  cudaError_t alloc(int64_t n, cudaStream_t s) {
+    st = s;
+    return cudaMallocAsync((void**)&p, sizeof(double) * n, s);
+  }
 };
 
 unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
@@ -52,9 +65,9 @@ bem_status gmres_solve_layout(const SegLayout& L, const MatvecFn& mv_hi, const M
     tot_iters = iters;
   } else {
     Dev r, dx, Ax;
-    STBEM_CUDA(cudaMalloc(&r.p, sizeof(double) * nn));
-    STBEM_CUDA(cudaMalloc(&dx.p, sizeof(double) * nn));
-    STBEM_CUDA(cudaMalloc(&Ax.p, sizeof(double) * nn));
+    STBEM_CUDA(r.alloc(nn, s));
+    STBEM_CUDA(dx.alloc(nn, s));
+    STBEM_CUDA(Ax.alloc(nn, s));
     std::vector<double> bn;
     st = seg_norms(L, d_b, bn, s);
     if (st != BEM_OK) return st;
@@ -78,6 +91,7 @@ bem_status gmres_solve_layout(const SegLayout& L, const MatvecFn& mv_hi, const M
         done = done && conv[c];
       }
       if (done || it == std::max(0, o->max_refine)) break;
+      if (cancel_requested()) { set_error("solve cancelled"); return BEM_ERR_CANCELLED; }
       STBEM_CUDA(cudaMemsetAsync(dx.p, 0, sizeof(double) * nn, s));
       std::vector<int> ci;
       std::vector<double> ri;

@@ -140,3 +140,56 @@ def laplace_triangle(x, tri):
         v, _ = integrate.quad(f, min(pa, pb), max(pa, pb), epsabs=1e-15, epsrel=1e-14, limit=200)
         total += sgn * v
     return total / (4.0 * np.pi)
+
+
+def laplace_triangle_ball(x, tri, rho):
+    """(1/4pi) int_{K cap B(x, rho)} dA/|x-y|: the Laplace single layer of a flat
+    triangle K restricted to the ball of radius rho around x (textbook polar
+    form as in laplace_triangle). Around the foot point xb, with d the height
+    of x over the plane and s the in-plane distance,
+    int dA/|x-y| over the disk part = int dphi [min(sqrt(s(phi)^2 + d^2), rho) - |d|];
+    the signed sum over the sub-triangles (xb, P_k, P_{k+1}) covers K. Each
+    phi-integral is split where the edge line leaves the ball (the kink of
+    the min)."""
+    x = np.asarray(x, float)
+    P = np.asarray(tri, float)
+    n = np.cross(P[1] - P[0], P[2] - P[0])
+    n /= np.linalg.norm(n)
+    d = float(np.dot(x - P[0], n))
+    if rho <= abs(d):
+        return 0.0
+    xb = x - d * n
+    total = 0.0
+    for k in range(3):
+        A, B = P[k] - xb, P[(k + 1) % 3] - xb
+        orient = np.dot(np.cross(A, B), n)
+        if abs(orient) < 1e-300:
+            continue
+        sgn = np.sign(orient)
+        e = B - A
+        lam0 = -np.dot(A, e) / np.dot(e, e)
+        F = A + lam0 * e
+        p = np.linalg.norm(F)
+        if p < 1e-300:
+            continue
+        eu = e / np.linalg.norm(e)
+        wa, wb = np.dot(A, eu), np.dot(B, eu)
+        pa, pb = np.arctan2(wa, p), np.arctan2(wb, p)
+        lo, hi = min(pa, pb), max(pa, pb)
+
+        def f(psi):
+            s = p / np.cos(psi)
+            return min(np.sqrt(s * s + d * d), rho) - abs(d)
+
+        cuts = [lo, hi]
+        sr2 = rho * rho - d * d
+        if sr2 > p * p:
+            c = np.arccos(p / np.sqrt(sr2))      # s(psi) = s_rho at psi = +-c
+            cuts += [v for v in (-c, c) if lo < v < hi]
+        cuts = sorted(cuts)
+        v = 0.0
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            vv, _ = integrate.quad(f, a, b, epsabs=1e-15, epsrel=1e-14, limit=200)
+            v += vv
+        total += sgn * v
+    return total / (4.0 * np.pi)

@@ -314,8 +314,10 @@ def test_sphere_closed_form_coarse():
     """P1 (discretisation level): on the sphere, V phi = 1/2 int_0^min(t,2) phi(t-r) dr
     for uniform phi; g = sin^2(pi t/2) on [0,2] has phi = pi sin(pi t). On the
     20-triangle icosahedron (edge ~ 1.05) the Galerkin solution follows it in
-    sign and shape with an L2(Sigma) error near 0.46; the finer levels are
-    checked on the GPU, where the error must fall with h."""
+    sign and shape with an L2(Sigma) error of 0.44 (first order in h: the
+    finer levels, checked on the GPU, fall to 0.18 and 0.09). A uniform scale
+    error of a few percent in A or b moves e out of [0.42, 0.46]; the column
+    sums above pin the entries to 1e-12."""
     m = inputs.sphere_mesh(0, 4, 2.0, 0.0)
     om = oracle.Mesh.from_spacetime(m)
     A = om.matrix(nthreads=os.cpu_count())
@@ -338,7 +340,7 @@ def test_sphere_closed_form_coarse():
             err2 += vol / 4 * (ex - w[j]) ** 2
             ref2 += vol / 4 * ex ** 2
     e = math.sqrt(err2 / ref2)
-    assert e < 0.55, e
+    assert 0.42 < e < 0.46, e
 
 
 def test_brute_force_apex_above_flat_top_face():
@@ -355,3 +357,64 @@ def test_brute_force_apex_above_flat_top_face():
         got = oracle.inner(x, tet)
         assert ref > 0.0
         assert abs(got - ref) <= 1e-9 * max(abs(ref), 1e-3), (j, got, ref)
+
+
+def _outer_faces(tet, sv):
+    """The two faces of a panel with nu_t != 0 (no vertical edge) as
+    (sign, 3 x 4 corners): sign -1 for the lower face (nu_t < 0: the vertical
+    edge's upper vertex lies off it), +1 for the upper face."""
+    dup = [k for k in range(4) if sum(sv[k] == sv[j] for j in range(4)) == 2]
+    top = max(dup, key=lambda k: tet[k, 0])
+    bot = min(dup, key=lambda k: tet[k, 0])
+    lower = tet[[k for k in range(4) if k != top]]
+    upper = tet[[k for k in range(4) if k != bot]]
+    return [(-1.0, lower), (1.0, upper)]
+
+
+def _midpoint_points(corners, m=3):
+    """Fig. int_tri_mid written out: centroids of the m^2 congruent
+    sub-triangles (upward ((i+1/3)/m, (j+1/3)/m), i+j <= m-1; downward
+    ((i+2/3)/m, (j+2/3)/m), i+j <= m-2)."""
+    pts = []
+    for off, top in [(1.0 / 3.0, m - 1), (2.0 / 3.0, m - 2)]:
+        for i in range(m):
+            for j in range(m):
+                if i + j <= top:
+                    a, b = (i + off) / m, (j + off) / m
+                    pts.append((1 - a - b) * corners[0] + a * corners[1] + b * corners[2])
+    return np.array(pts)
+
+
+def test_column_sums_are_truncated_laplace_layers():
+    """Entry level pin (eq. int_bform, Fig. int_tri_mid, eq. slp): the panels
+    over one spatial triangle K_J tile K_J x [0, T], so for an apex (t, x) the
+    inner integrals of the whole column sum to
+    (1/4pi) int_{K_J} 1[0 < t - |x-y| < T] / |x-y| dA, the Laplace single layer
+    of K_J restricted to the ball |x - y| < t (t <= T). With nu_{F,t}|F| = -|K_I|
+    on the lower face and +|K_I| on the upper one,
+        sum_{j over K_J} A_ij = |K_I| / m_Q^2 (sum_{q, lower} L(x_q) - sum_{q, upper} L(x_q)).
+    A wrong weight, sign, outer point or a dropped inner term fails it. (Where
+    every outer point sees all of K_J the two sums cancel: the static field
+    has no time derivative; the pairs below include many that do not.)"""
+    m = inputs.sphere_mesh(1, 4, 2.0, 0.2, seed=3)
+    om = oracle.Mesh.from_spacetime(m)
+    X = m.stv_xyzt()
+    per_col = 3 * 4
+    sums, refs = [], []
+    for i in (200, 455, 610, 900, 17, 301):
+        tet = X[m.tets[i]]
+        K_I = m.svert[m.tri[i // per_col]]
+        area = 0.5 * np.linalg.norm(np.cross(K_I[1] - K_I[0], K_I[2] - K_I[0]))
+        faces = _outer_faces(tet, m.stv_sv[m.tets[i]])
+        for J in (0, 7, 33, 55, 79):
+            pairs = np.array([(i, j) for j in range(J * per_col, (J + 1) * per_col)], dtype=np.int32)
+            sums.append(om.entries(pairs, nthreads=os.cpu_count()).sum())
+            ref = 0.0
+            for sign, corners in faces:
+                for xq in _midpoint_points(corners):
+                    ref -= sign * _brute.laplace_triangle_ball(xq[1:], m.svert[m.tri[J]], xq[0])
+            refs.append(ref * area / 9.0)
+    sums, refs = np.array(sums), np.array(refs)
+    scale = np.abs(refs).max()
+    assert np.count_nonzero(np.abs(refs) > 1e-6 * scale) >= 10
+    assert np.abs(sums - refs).max() <= 1e-12 * scale, np.abs(sums - refs).max() / scale
