@@ -35,6 +35,7 @@ METRIC = "retarded-V pair integrals/s"
 WORKLOADS = {
     "c2": "icosphere L3 (1280 triangles), T=4, 32 slabs, +-20% time jitter: 122,880 panels; m_Q=3",
     "l3x16": "icosphere L3 (1280 triangles), T=4, 16 slabs, +-20% time jitter: 61,440 panels; m_Q=3",
+    "l3x8": "icosphere L3 (1280 triangles), T=4, 8 slabs, +-20% time jitter: 30,720 panels; m_Q=3",
     "l2x8": "icosphere L2 (320 triangles), T=2, 8 slabs, +-20% time jitter: 7,680 panels; m_Q=3",
 }
 WORKLOAD = WORKLOADS["c2"]
@@ -198,10 +199,15 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     prec = args.precision
+    ctx0 = stb.Context(local if dist else 0)
+    alu = ctx0.alu_peaks()      # FP32 / FP64 FMA rates of this GPU, before the timed region
+    ctx0.close()
     if args.workload == "c2":
         m = inputs.workload_c2(seed=1 + rank)
     elif args.workload == "l3x16":
         m = inputs.sphere_mesh(3, 16, 4.0, 0.2, seed=1 + rank)
+    elif args.workload == "l3x8":
+        m = inputs.sphere_mesh(3, 8, 4.0, 0.2, seed=1 + rank)
     else:
         m = inputs.sphere_mesh(2, 8, 2.0, 0.2, seed=3)
     ctx = stb.Context(local if dist else 0)
@@ -209,6 +215,7 @@ def run_ours(args):
     op = stb.Operator(ctx, mesh, prec, store_fp32=True)
     st = op.stats()
     nnz = st["nnz"]
+    n_inner = op.inner_integrals()
     stream = torch.cuda.Stream()
     for _ in range(args.warmup):
         op.reassemble(stream)
@@ -251,7 +258,8 @@ def run_ours(args):
     t_e2e, _ = aggregate(t_e2e, 0, "cuda")
     d2h = m.n_tet * 8 + m.n_tet * 8  # rhs vector and density back to the host
 
-    multi = multi_rhs_leg(op, m, args) if args.multi_rhs > 0 else None
+    acc = accuracy_leg(ctx, mesh, op, m, args) if (args.accuracy and rank == 0) else None
+    multi = multi_rhs_leg(op, m, args, ref=acc.pop("_W64") if acc else None) if args.multi_rhs > 0 else None
     serving = serving_leg(ctx, args) if (args.serve_requests > 0 and rank == 0) else None
     batched = batch_leg(ctx, args) if (args.batch > 0 and rank == 0) else None
 
@@ -264,16 +272,25 @@ def run_ours(args):
     pk = peaks()
     prof = load_profile_summary()
     roof = None
-    if prof:
-        flops = prof["fp32_flops_per_pair"] * nnz
-        achieved = flops / (quad_ms / 1e3) / 1e12
-        peak = prof["fp32_peak_tflops"]
-        traffic = prof["dram_bytes_per_pair"] * nnz if prof.get("dram_bytes_per_pair") else None
-        roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
+    inner_per_s = n_inner / (quad_ms / 1e3)
+    if prof and "fp32_flops_per_inner" in prof:
+        # executed flops per inner integral of the quadrature kernel, from an ncu
+        # capture of the same kernel on a mesh whose values exceed L2 (level-3
+        # sphere, 8 slabs), times this run's inner integrals, over the kernel's
+        # CUDA-event time; peaks measured on this GPU in this run
+        f32 = prof["fp32_flops_per_inner"] * n_inner / (quad_ms / 1e3) / 1e12
+        f64 = prof["fp64_flops_per_inner"] * n_inner / (quad_ms / 1e3) / 1e12
+        traffic = prof["dram_bytes_per_inner"] * n_inner if prof.get("dram_bytes_per_inner") else None
+        roof = {"bound": "alu", "achieved": round(f32, 3), "peak": round(alu["fp32_tflops"], 2), "unit": "TFLOP/s",
+                "frac": round(f32 / alu["fp32_tflops"], 4), "traffic": traffic,
                 "kernel": "k_quad_blocks<mixed>",
-                "note": "executed FP32 flops per pair from an ncu capture of the same kernel on a smaller mesh, "
-                        "scaled by admissible pairs; peak = 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+                "fp64": {"achieved": round(f64, 4), "peak": round(alu["fp64_tflops"], 3), "unit": "TFLOP/s",
+                         "frac": round(f64 / alu["fp64_tflops"], 4)},
+                "inner_integrals_per_launch": n_inner,
+                "note": "achieved = executed FP32 (FP64) flops per inner integral from ncu (SASS op counters, "
+                        "FFMA counted 2) on the level-3 sphere with 8 slabs x inner integrals of this launch / "
+                        "its CUDA-event time; peak = FMA rate measured on this GPU in this run (bem_alu_peaks; "
+                        "152 SMs x 128 lanes x 2 x 2.07 GHz = 80.5 TFLOP/s nominal)"}
     cb = cpu_baseline(m, seconds=args.cpu_seconds) if args.cpu_seconds > 0 else None
     vbytes = st["stored"] * (4 if prec == "mixed" else 12)  # FP32 values; FP64 operators also keep FP64
     out = {
@@ -281,6 +298,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if prec == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "precision": prec, "pairs_per_rank": nnz,
+                   "inner_integrals_per_rank": n_inner,
                    "stored_values": st["stored"], "parallelism": f"independent meshes per rank (x{world})",
                    "l2": f"each step writes the {vbytes / 1e9:.2f} GB value array: "
                          + ("larger than L2" if vbytes > L2_BYTES else "smaller than L2 (profiling case)")},
@@ -294,10 +312,13 @@ def run_ours(args):
         "clocks": clk.summary(),
         "roofline": roof,
         "cpu_baseline": cb,
+        "accuracy": acc,
         "multi_rhs": multi,
         "serving": serving,
         "batch": batched,
-        "peaks": {"hbm_gbs": pk.get("hbm_gbs"), "bf16_tflops": pk.get("bf16_tflops")},
+        "inner_integrals_per_s": inner_per_s,
+        "peaks": {"hbm_gbs": pk.get("hbm_gbs"), "bf16_tflops": pk.get("bf16_tflops"),
+                  "fp32_tflops_measured": alu["fp32_tflops"], "fp64_tflops_measured": alu["fp64_tflops"]},
     }
     print(json.dumps(out), flush=True)
     if dist:
@@ -305,12 +326,59 @@ def run_ours(args):
         tdist.destroy_process_group()
 
 
-def multi_rhs_leg(op, m, args):
+def accuracy_leg(ctx, mesh, op, m, args):
+    """The reduced-precision form against the FP64 operator on the same mesh
+    (the GPU FP64 path, itself checked against the oracle to 1e-11 in the
+    tests): the FP64 operator is assembled, the single-RHS solution of the
+    benchmark's data is compared with its FP64 GMRES solution, and the 64-RHS
+    reference (pulses with centres in [1, 2]) is the refinement whose
+    residual uses the FP64 operator (bem_solve_refined), which converges to
+    the FP64 operator's solution."""
+    import torch
+    import paper_2103_16841_gb300 as stb
+    from paper_2103_16841_gb300 import inputs
+    t0 = time.perf_counter()
+    op64 = stb.Operator(ctx, mesh, "fp64", store_fp32=False)
+    torch.cuda.synchronize()
+    out = {"fp64_operator_s": round(time.perf_counter() - t0, 2),
+           "fp64_quadrature_ms": round(op64.timings()["quadrature_ms"], 1)}
+    b = op.rhs(stb.DATA_PULSE, inputs.pulse_params(1, seed=2, fixed_c=1.5))[:, 0]
+    w64, i64 = op64.solve(b, tol=1e-12, restart=100, maxit=4000, inner="fp64", allow_unconverged=True)
+    wm, im = op.solve(b, tol=1e-8, restart=50, maxit=400, inner="fp32", max_refine=8, allow_unconverged=True)
+    t1 = time.perf_counter()
+    wr, ir = op.solve_refined(op64, b, tol=1e-10, restart=50, maxit=600, inner="fp32", max_refine=20,
+                              allow_unconverged=True)
+    t_ref = time.perf_counter() - t1
+    rel = lambda w: float(np.linalg.norm(w - w64) / np.linalg.norm(w64))
+    out["single_rhs"] = {"fp64_gmres_iterations": i64[0]["iterations"],
+                         "mixed_fp32_inner_tol_1e-8": {"rel_error_vs_fp64_operator": rel(wm),
+                                                       "rel_residual": im[0]["rel_residual"]},
+                         "mixed_with_fp64_residual_tol_1e-10": {"rel_error_vs_fp64_operator": rel(wr),
+                                                                "seconds": round(t_ref, 2),
+                                                                "refinements": ir[0]["refinements"]}}
+    W64 = None
+    if args.multi_rhs > 0:
+        prm = inputs.pulse_params(args.multi_rhs, seed=2)
+        B = op.rhs(stb.DATA_PULSE, prm)
+        t1 = time.perf_counter()
+        W64, info = op.solve_refined(op64, B, tol=1e-11, restart=50, maxit=800, inner="tf32", max_refine=30,
+                                     allow_unconverged=True)
+        out["multi_rhs_reference"] = {"how": "TF32 inner solves on the mixed operator, FP64 residual of the FP64 "
+                                             "operator, tol 1e-11", "seconds": round(time.perf_counter() - t1, 2),
+                                      "converged": int(sum(i["converged"] for i in info)),
+                                      "rel_residual_max": float(max(i["rel_residual"] for i in info))}
+    op64.close()
+    out["_W64"] = W64
+    return out
+
+
+def multi_rhs_leg(op, m, args, ref=None):
     """Many right-hand sides on the assembled operator: the block matvec in
     FP32 (CUDA cores), TF32 and BF16 (tensor cores) with the values read once
     per product, and GMRES with TF32 / BF16 inner solves plus FP64
-    refinement to 1e-8; errors per RHS against the TF32-inner solution refined
-    to 1e-12 in FP64."""
+    refinement to 1e-8; errors per RHS against the FP64 operator's solution
+    (from the accuracy leg) when given, else against the TF32-inner solution
+    of the same operator refined to 1e-12."""
     import torch
     import paper_2103_16841_gb300 as stb
     from paper_2103_16841_gb300 import inputs
@@ -362,10 +430,12 @@ def multi_rhs_leg(op, m, args):
                                "passes_over_values": math.ceil(nrhs / 4) if dt == "fp32" else math.ceil(nrhs / 64),
                                "note": "includes the FP64 <-> packed-operand conversions and the caller-order "
                                        "permutations of bem_matvec_dtype"}
-    ref = None
-    # the reference: TF32 inner solves refined in FP64 to 1e-12 (the FP64
-    # solution of the same operator); then each arithmetic to 1e-8
-    for key, inner, tol in [("reference_tf32_1e-12", "tf32", 1e-12), ("tf32", "tf32", 1e-8), ("bf16", "bf16", 1e-8)]:
+    runs = [("tf32", "tf32", 1e-8), ("bf16", "bf16", 1e-8)]
+    key_err = "rel_error_vs_fp64_operator_per_rhs"
+    if ref is None:
+        runs = [("reference_tf32_1e-12", "tf32", 1e-12)] + runs
+        key_err = "rel_error_vs_same_operator_refined_per_rhs"
+    for key, inner, tol in runs:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         w, info = op.solve(b, tol=tol, restart=50, maxit=600, inner=inner, max_refine=30, allow_unconverged=True)
@@ -378,7 +448,7 @@ def multi_rhs_leg(op, m, args):
             ref = w
         else:
             err = np.linalg.norm(w - ref, axis=0) / np.linalg.norm(ref, axis=0)
-            rec["rel_error_vs_fp64_refined_per_rhs"] = [float("%.3e" % e) for e in err]
+            rec[key_err] = [float("%.3e" % e) for e in err]
             rec["rel_error_max"] = float(err.max())
         out["solves"][key] = rec
     return out
@@ -419,9 +489,12 @@ def serving_leg(ctx, args):
     """Poisson stream of Dirichlet solves through the continuous-batching
     server: the mixed-precision form (FP32 quadrature, FP32 inner GMRES, FP64
     refinement) against the plain FP64 path (FP64 quadrature and GMRES), on
-    the same trace and server settings. Requests are drawn uniformly from
-    icosphere levels x slab counts x right-hand-side counts (T = 4, +-20%
-    jitter, pulse data); latency = submission to completion."""
+    the same trace and server settings, both keeping assembled operators
+    resident (a later request on the same mesh skips the assembly). Requests
+    are drawn uniformly from icosphere levels x slab counts x right-hand-side
+    counts (T = 4, +-20% jitter, one seeded mesh per (level, slabs) shape,
+    pulse data with per-request seeds); latency = submission to completion.
+    Each request's mixed-precision density is compared with its FP64 one."""
     import paper_2103_16841_gb300 as stb
     from paper_2103_16841_gb300 import inputs
     rng = np.random.default_rng(4)
@@ -430,16 +503,20 @@ def serving_leg(ctx, args):
     nrhs_set = [1, 4, 16]
     n = args.serve_requests
     arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, n))
+    shapes = {}
     reqs = []
     for k in range(n):
         lv, sl, nr = int(rng.choice(levels)), int(rng.choice(slabs)), int(rng.choice(nrhs_set))
-        m = inputs.sphere_mesh(lv, sl, 4.0, 0.2, seed=1000 + k)
-        reqs.append((m, inputs.pulse_params(nr, seed=2000 + k), f"L{lv}x{sl}x{nr}"))
+        if (lv, sl) not in shapes:
+            shapes[(lv, sl)] = inputs.sphere_mesh(lv, sl, 4.0, 0.2, seed=1000 + 10 * lv + sl)
+        reqs.append((shapes[(lv, sl)], inputs.pulse_params(nr, seed=2000 + k), f"L{lv}x{sl}x{nr}"))
     out = {"requests": n, "poisson_rate_per_s": args.serve_rate, "slots": args.serve_slots,
-           "mix": {"levels": levels, "slabs": slabs, "nrhs": nrhs_set}, "tol": 1e-8, "paths": {}}
+           "mix": {"levels": levels, "slabs": slabs, "nrhs": nrhs_set}, "mesh_shapes_in_trace": len(shapes),
+           "tol": 1e-8, "resident_operators": True, "paths": {}}
+    dens = {}
     for name, prec, inner in [("mixed", "mixed", "fp32"), ("fp64", "fp64", "fp64")]:
         srv = stb.Server(ctx, max_slots=args.serve_slots, precision=prec, inner=inner, tol=1e-8, restart=50,
-                         maxit=3000, max_refine=12)
+                         maxit=3000, max_refine=12, cache_operators=True)
         t0 = time.perf_counter()
         tickets = []
         for (m, prm, _), ta in zip(reqs, arrivals):
@@ -453,13 +530,20 @@ def serving_leg(ctx, args):
         srv.close()
         lat = np.array([res[t]["latency_ms"] for t in tickets])
         ok = sum(res[t]["status"] == 0 for t in tickets)
+        dens[name] = [res[t]["w"] for t in tickets]
         out["paths"][name] = {
             "precision": prec, "inner": inner, "completed": int(ok),
             "solves_per_s": round(float(st["solves_per_s"]), 3),
             "p50_ms": round(float(np.percentile(lat, 50)), 1), "p99_ms": round(float(np.percentile(lat, 99)), 1),
             "mean_ms": round(float(lat.mean()), 1), "wall_s": round(t_end - t0, 2),
-            "peak_running": int(st["peak_running"]),
+            "peak_running": int(st["peak_running"]), "cache_hits": int(st["cache_hits"]),
             "rel_residual_max": float(max(res[t]["rel_residual"] for t in tickets))}
+    errs = []
+    for wm, w64 in zip(dens["mixed"], dens["fp64"]):
+        if wm is not None and w64 is not None:
+            errs.append(float((np.linalg.norm(wm - w64, axis=1) / np.linalg.norm(w64, axis=1)).max()))
+    out["mixed_vs_fp64_rel_error_per_request_max"] = max(errs) if errs else None
+    out["mixed_vs_fp64_rel_error_per_request_median"] = float(np.median(errs)) if errs else None
     mx, fp = out["paths"]["mixed"], out["paths"]["fp64"]
     out["speedup_solves_per_s"] = round(mx["solves_per_s"] / max(fp["solves_per_s"], 1e-12), 2)
     return out
@@ -484,19 +568,23 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", dest="cpu_seconds", type=float, default=12.0)
+    ap.add_argument("--accuracy", type=int, default=1,
+                    help="1: assemble the FP64 operator of the same mesh and report the mixed form's errors "
+                         "against its solutions (0: skip)")
     ap.add_argument("--multi-rhs", dest="multi_rhs", type=int, default=64,
                     help="right-hand sides of the multi-RHS leg (0: skip)")
     ap.add_argument("--batch", type=int, default=64,
                     help="small scatterers of the batch leg (0: skip; 512 is the full batch)")
-    ap.add_argument("--serve-requests", dest="serve_requests", type=int, default=16,
+    ap.add_argument("--serve-requests", dest="serve_requests", type=int, default=24,
                     help="requests of the serving leg (0: skip)")
-    ap.add_argument("--serve-rate", dest="serve_rate", type=float, default=2.0, help="Poisson arrivals per second")
+    ap.add_argument("--serve-rate", dest="serve_rate", type=float, default=1.0, help="Poisson arrivals per second")
     ap.add_argument("--serve-slots", dest="serve_slots", type=int, default=4)
-    ap.add_argument("--serve-full", dest="serve_full", action="store_true",
-                    help="draw from levels 1-3 and 8/16/32 slabs (the full serving mix; minutes on the FP64 path)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "l3x16", "l2x8"],
-                    help="l3x16 / l2x8: the level-3 sphere with 16 slabs (T = 4) / the level-2 sphere with "
-                         "8 slabs (T = 2), jittered, for profiler captures only")
+    ap.add_argument("--serve-small", dest="serve_full", action="store_false",
+                    help="draw from levels 1-2 and 8/16 slabs only (default: the full mix, levels 1-3 x 8/16/32 "
+                         "slabs x 1/4/16 RHS)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "l3x16", "l3x8", "l2x8"],
+                    help="l3x16 / l3x8 / l2x8: the level-3 sphere with 16 or 8 slabs (T = 4) / the level-2 sphere "
+                         "with 8 slabs (T = 2), jittered, for profiler captures only")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

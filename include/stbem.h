@@ -171,6 +171,12 @@ bem_status bem_operator_create(bem_context* ctx, const bem_mesh* mesh, const bem
 bem_status bem_operator_stats(const bem_operator* op, int64_t* nnz_pattern, int64_t* stored_values,
                               int64_t* n_blocks, double* assemble_ms);
 
+/* Algorithmic work of one assembly: inner_integrals = m_Q^2 x the number of
+ * (test face with nu_t != 0, trial panel) pairs in the sparsity pattern, i.e.
+ * the values V 1_{sigma_j}(x_{F,q}) of eq. int_bform the quadrature evaluates
+ * (a face shared by two test panels counted once). Counted by the pattern pass. */
+bem_status bem_operator_work(const bem_operator* op, int64_t* inner_integrals);
+
 /* Scans the stored values on the device: number of non-finite values (NaN,
  * Inf) and the largest magnitude. A healthy operator has n_nonfinite = 0. */
 bem_status bem_operator_check(const bem_operator* op, int64_t* n_nonfinite, double* max_abs);
@@ -311,6 +317,17 @@ typedef struct {
 bem_status bem_solve(bem_operator* op, const double* b, double* w, int32_t nrhs, const bem_solve_opts* opts,
                      bem_solve_info* info);
 
+/* Iterative refinement with an FP64-accurate residual (precision pattern of
+ * the reduced-precision form): solves op_hi w = b, where the outer residual
+ * r = b - A_hi w is formed with op_hi's values in FP64 (an FP64 operator, or
+ * a matrix-free FP64 one) and the corrections come from GMRES on op_lo (a
+ * MIXED operator) in opts->inner_dtype (FP32, TF32 or BF16). The refinement
+ * converges to op_hi's solution, so the FP32 quadrature error of op_lo limits
+ * only the speed of convergence, not the accuracy. Both operators must be
+ * built on the same mesh handle. Host arrays as bem_solve; info [nrhs]. */
+bem_status bem_solve_refined(const bem_operator* op_hi, bem_operator* op_lo, const double* b, double* w,
+                             int32_t nrhs, const bem_solve_opts* opts, bem_solve_info* info);
+
 /* Same on device arrays, enqueued on `stream`; blocks until done. */
 bem_status bem_solve_device(bem_operator* op, const double* b_dev, double* w_dev, int32_t nrhs,
                             const bem_solve_opts* opts, bem_solve_info* info, void* stream);
@@ -391,7 +408,11 @@ void bem_batch_destroy(bem_batch* batch);
  * slot's share) completes with BEM_ERR_OUT_OF_MEMORY. Slots run
  * concurrently, so the kernels of different requests overlap on the device;
  * every request's arithmetic is the same alone and in a mix (its reductions
- * have a fixed order), so its result does not depend on the other requests. */
+ * have a fixed order), so its result does not depend on the other requests.
+ * Device memory of a request (right-hand side, solution, GMRES workspace) is
+ * allocated and released stream-ordered on its slot's stream, so one
+ * request's release does not stall the others. With cache_operators = 1 the
+ * assembled operators stay resident (see bem_server_opts). */
 typedef struct bem_server bem_server;
 
 typedef struct {
@@ -401,6 +422,11 @@ typedef struct {
   int32_t inner_dtype;   /* bem_solve_opts.inner_dtype (BEM_DTYPE_FP64 for the plain FP64 path) */
   int32_t restart, maxit, max_refine;
   double tol;            /* relative residual target of every solve */
+  int32_t cache_operators;/* 1: keep each assembled operator (mesh, sparsity, values) resident after its
+                            request, keyed by the request's mesh arrays; a later request on the same mesh
+                            reuses it and reserves only its solver workspace. Cached operators hold pool
+                            bytes and are evicted least recently used when an admission needs the room. */
+  int32_t reserved0;
 } bem_server_opts;
 
 typedef struct {         /* one request: a space-time mesh (as bem_mesh_create) and its data */
@@ -429,6 +455,8 @@ typedef struct {
   double queue_ms;       /* submit -> taken by a slot */
   double latency_ms;     /* submit -> completed */
   int64_t reserved_bytes;/* HBM reserved at admission */
+  int32_t cache_hit;     /* 1: the request reused a resident operator (no assembly) */
+  int32_t reserved0;
 } bem_completion;
 
 typedef struct {
@@ -438,6 +466,8 @@ typedef struct {
   int64_t peak_reserved_bytes;
   double solves_per_s;   /* completed / (last completion - first submission) */
   double p50_ms, p99_ms, mean_ms, max_ms;  /* latency over completed requests */
+  int64_t cache_hits;    /* requests served by a resident operator */
+  int64_t cached_operators, cached_bytes;  /* operators resident now and the pool bytes they hold */
 } bem_server_stats;
 
 /* Inputs of bem_server_submit are copied; the call never blocks on the GPU. */

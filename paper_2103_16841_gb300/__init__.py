@@ -120,6 +120,12 @@ class Operator:
                                                   _lib.dptr(ms)))
         return {"nnz": int(a[0]), "stored": int(a[1]), "blocks": int(a[2]), "assemble_ms": float(ms[0])}
 
+    def inner_integrals(self):
+        """Inner integrals of one assembly (bem_operator_work)."""
+        n = np.zeros(1, dtype=np.int64)
+        _lib.check(self.ctx._L.bem_operator_work(self.h, _lib.lptr(n)))
+        return int(n[0])
+
     def check(self):
         """(number of non-finite stored values, largest |value|)"""
         n = np.zeros(1, dtype=np.int64)
@@ -198,6 +204,24 @@ class Operator:
                                                     _lib.dptr(b)))
         b = b.reshape(nrhs, self.n).T.copy()
         return b[:, 0] if vec else b
+
+    def solve_refined(self, op_hi, b, tol=1e-10, restart=50, maxit=2000, inner="tf32", max_refine=20,
+                      allow_unconverged=False):
+        """bem_solve_refined: refinement with op_hi's FP64 residual and inner
+        solves on this (mixed) operator. Host b [n] or [n, nrhs]."""
+        b = np.asarray(b, dtype=np.float64)
+        vec = b.ndim == 1
+        B = np.ascontiguousarray((b[:, None] if vec else b).T)
+        nrhs = B.shape[0]
+        W = np.zeros_like(B)
+        o = _lib.SolveOpts(float(tol), int(restart), int(maxit), _lib.DTYPE[inner], int(max_refine))
+        info = (_lib.SolveInfo * nrhs)()
+        st = self.ctx._L.bem_solve_refined(op_hi.h, self.h, _lib.dptr(B), _lib.dptr(W), nrhs, ctypes.byref(o), info)
+        _lib.check(st, allow=(4,) if allow_unconverged else ())
+        infos = [{"iterations": i.iterations, "refinements": i.refinements, "converged": bool(i.converged),
+                  "rel_residual": i.rel_residual, "solve_ms": i.solve_ms} for i in info]
+        w = W.T.copy()
+        return (w[:, 0] if vec else w), infos
 
     def solve_async(self, b, w, tol=1e-8, restart=50, maxit=2000, inner="fp64", max_refine=10, stream=None):
         """Starts bem_solve_async on contiguous CUDA float64 tensors b, w of shape
@@ -379,10 +403,10 @@ class Server:
     [nrhs, n_tet] (caller panel order) and their timings."""
 
     def __init__(self, ctx: Context, hbm_budget=0, max_slots=4, precision="mixed", inner="fp32", tol=1e-8,
-                 restart=50, maxit=2000, max_refine=10):
+                 restart=50, maxit=2000, max_refine=10, cache_operators=False):
         self.ctx = ctx
         o = _lib.ServerOpts(int(hbm_budget), int(max_slots), _lib.PREC[precision], _lib.DTYPE[inner],
-                            int(restart), int(maxit), int(max_refine), float(tol))
+                            int(restart), int(maxit), int(max_refine), float(tol), int(bool(cache_operators)), 0)
         h = ctypes.c_void_p()
         _lib.check(ctx._L.bem_server_create(ctx.h, ctypes.byref(o), ctypes.byref(h)))
         self.h = h
@@ -416,7 +440,7 @@ class Server:
             out.append({"ticket": int(c.ticket), "status": int(c.status), "w": w, "iterations": int(c.iterations),
                         "refinements": int(c.refinements), "rel_residual": float(c.rel_residual),
                         "queue_ms": float(c.queue_ms), "latency_ms": float(c.latency_ms),
-                        "reserved_bytes": int(c.reserved_bytes)})
+                        "reserved_bytes": int(c.reserved_bytes), "cache_hit": bool(c.cache_hit)})
             _lib.check(self.ctx._L.bem_server_release(self.h, c.ticket))
         return out
 
@@ -460,6 +484,11 @@ def inner_potentials(ctx: Context, x4, tets, tet_sv, precision="fp64", n_theta=0
     return out
 
 
+# cudaStreamLegacy: the legacy default stream named explicitly (a NULL stream
+# argument means the library context's own stream)
+_CUDA_STREAM_LEGACY = 1
+
+
 def _stream_ptr(stream):
     """cudaStream_t of `stream`; None gives torch's current stream, so that the
     library's work is ordered with the torch operations around the call."""
@@ -468,6 +497,5 @@ def _stream_ptr(stream):
         if not torch.cuda.is_available():
             return None
         stream = torch.cuda.current_stream()
-    if hasattr(stream, "cuda_stream"):
-        return ctypes.c_void_p(stream.cuda_stream)
-    return ctypes.c_void_p(int(stream))
+    h = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    return ctypes.c_void_p(h if h else _CUDA_STREAM_LEGACY)

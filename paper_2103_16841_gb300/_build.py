@@ -17,6 +17,12 @@ LIB = os.path.join(BUILD, "libstbem.so")
 SOURCES = ["stbem_core.cu", "stbem_matvec.cu", "stbem_solver.cu", "stbem_gmres.cu", "stbem_capi.cu", "stbem_noalloc.cu", "stbem_server.cu", "stbem_batch.cu", "stbem_peaks.cu"]
 HEADERS = ["stbem_quad.cuh", "stbem_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The quadrature translation unit: FP32 division and square root to within a
+# few ulp (the hardware approximations) and FP32 denormals flushed. The mixed
+# quadrature's error target is 1e-7 relative, formed from cancellation-free
+# expressions, and the FP64 arithmetic (cone geometry, the FP64 path, the
+# sparsity contract) is unaffected by these flags.
+SOURCE_FLAGS = {"stbem_core.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
 
 
 def nvcc() -> str:
@@ -35,7 +41,8 @@ def _stale(obj, src):
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    deps = [src] + [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(HERE, "..", "include", "stbem.h")]
+    deps = [src, os.path.abspath(__file__)] + [os.path.join(CSRC, h) for h in HEADERS] + \
+        [os.path.join(HERE, "..", "include", "stbem.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
@@ -49,7 +56,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
         obj = os.path.join(BUILD, s.replace(".cu", ".o"))
         objs.append(obj)
         if force or _stale(obj, src):
-            extra = ["-Xptxas", "-v"] if ptxas_v else []
+            extra = (["-Xptxas", "-v"] if ptxas_v else []) + SOURCE_FLAGS.get(s, [])
             jobs.append([nv, *_flags(extra), "-c", src, "-o", obj])
 
     def run(cmd):

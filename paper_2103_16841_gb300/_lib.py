@@ -27,9 +27,9 @@ DATA_PULSE = 1
 EXPORTS = [
     "bem_context_create", "bem_context_destroy", "bem_last_error", "bem_version", "bem_alu_peaks",
     "bem_mesh_create", "bem_mesh_create_prisms", "bem_mesh_info", "bem_mesh_destroy",
-    "bem_operator_create", "bem_operator_stats", "bem_operator_check", "bem_operator_timings", "bem_operator_reassemble", "bem_operator_export_pattern", "bem_operator_pattern_rows",
+    "bem_operator_create", "bem_operator_stats", "bem_operator_check", "bem_operator_work", "bem_operator_timings", "bem_operator_reassemble", "bem_operator_export_pattern", "bem_operator_pattern_rows",
     "bem_operator_export_dense", "bem_operator_entries", "bem_operator_destroy",
-    "bem_rhs", "bem_rhs_points", "bem_rhs_from_samples", "bem_matvec", "bem_matvec_dtype", "bem_matvec_noalloc", "bem_solve", "bem_solve_device",
+    "bem_rhs", "bem_rhs_points", "bem_rhs_from_samples", "bem_matvec", "bem_matvec_dtype", "bem_matvec_noalloc", "bem_solve", "bem_solve_refined", "bem_solve_device",
     "bem_solve_async", "bem_request_wait", "bem_request_cancel", "bem_request_destroy", "bem_inner_potentials",
     "bem_batch_create", "bem_batch_stats", "bem_batch_solve", "bem_batch_destroy",
     "bem_server_create", "bem_server_submit", "bem_server_poll", "bem_server_release", "bem_server_stats_get",
@@ -61,7 +61,8 @@ class SolveInfo(ctypes.Structure):
 class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_int64), ("max_slots", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("inner_dtype", ctypes.c_int32), ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
-                ("max_refine", ctypes.c_int32), ("tol", ctypes.c_double)]
+                ("max_refine", ctypes.c_int32), ("tol", ctypes.c_double), ("cache_operators", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32)]
 
 
 class Job(ctypes.Structure):
@@ -76,7 +77,8 @@ class Completion(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("nrhs", ctypes.c_int32),
                 ("n_tet", ctypes.c_int64), ("w", ctypes.POINTER(ctypes.c_double)),
                 ("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32), ("rel_residual", ctypes.c_double),
-                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("reserved_bytes", ctypes.c_int64)]
+                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("reserved_bytes", ctypes.c_int64),
+                ("cache_hit", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -84,7 +86,8 @@ class ServerStats(ctypes.Structure):
                 ("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("peak_running", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("peak_reserved_bytes", ctypes.c_int64),
                 ("solves_per_s", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
-                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double)]
+                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("cache_hits", ctypes.c_int64),
+                ("cached_operators", ctypes.c_int64), ("cached_bytes", ctypes.c_int64)]
 
 
 _lib = None
@@ -126,6 +129,7 @@ def load(build_if_missing: bool = False):
     L.bem_operator_reassemble.argtypes = [VP, VP]
     L.bem_operator_timings.argtypes = [VP, D]
     L.bem_operator_check.argtypes = [VP, I64, D]
+    L.bem_operator_work.argtypes = [VP, I64]
     L.bem_operator_export_pattern.argtypes = [VP, I64, I32]
     L.bem_operator_export_dense.argtypes = [VP, D]
     L.bem_operator_pattern_rows.argtypes = [VP, ctypes.c_int64, I32, ctypes.c_int64, I64, I32]
@@ -139,6 +143,8 @@ def load(build_if_missing: bool = False):
     L.bem_matvec_dtype.argtypes = [VP, VP, VP, ctypes.c_int32, ctypes.c_int32, VP]
     L.bem_matvec_noalloc.argtypes = [VP, VP, VP, ctypes.c_int32, VP]
     L.bem_solve.argtypes = [VP, D, D, ctypes.c_int32, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]
+    L.bem_solve_refined.argtypes = [VP, VP, D, D, ctypes.c_int32, ctypes.POINTER(SolveOpts),
+                                    ctypes.POINTER(SolveInfo)]
     L.bem_solve_device.argtypes = [VP, VP, VP, ctypes.c_int32, ctypes.POINTER(SolveOpts),
                                    ctypes.POINTER(SolveInfo), VP]
     L.bem_solve_async.argtypes = [VP, VP, VP, ctypes.c_int32, ctypes.POINTER(SolveOpts), VP, ctypes.POINTER(VP)]

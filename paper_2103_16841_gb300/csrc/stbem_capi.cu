@@ -452,7 +452,10 @@ bem_status assemble(bem_operator* op, cudaStream_t s, bool first) {
   std::vector<int64_t> bnnz(nb);
   STBEM_CUDA(cudaMemcpyAsync(bw.data(), op->d_bw, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, s));
   STBEM_CUDA(cudaMemcpyAsync(bnnz.data(), op->d_bnnz, sizeof(int64_t) * nb, cudaMemcpyDeviceToHost, s));
+  unsigned long long n_inner = 0;
+  STBEM_CUDA(cudaMemcpyAsync(&n_inner, op->d_counter + 1, sizeof(n_inner), cudaMemcpyDeviceToHost, s));
   STBEM_CUDA(cudaStreamSynchronize(s));
+  op->n_inner = (int64_t)n_inner;
   TRY(op_layout(op, bw.data(), bnnz.data(), first, true, s));
   STBEM_CUDA(cudaEventRecord(ec, s));
   if (!op->opts.matrix_free) TRY(op_quadrature(op, s));
@@ -529,6 +532,12 @@ bem_status stbem::operator_create(bem_context* ctx, const bem_mesh* mesh, const 
 }
 
 extern "C" {
+
+bem_status bem_operator_work(const bem_operator* op, int64_t* inner_integrals) {
+  if (!op || !inner_integrals) { set_error("bem_operator_work: invalid argument"); return BEM_ERR_INVALID_ARG; }
+  *inner_integrals = op->n_inner;
+  return BEM_OK;
+}
 
 bem_status bem_operator_check(const bem_operator* op, int64_t* n_nonfinite, double* max_abs) {
   if (op && op->opts.matrix_free) {
@@ -870,6 +879,49 @@ bem_status bem_solve_device(bem_operator* op, const double* b_dev, double* w_dev
   bem_status st = gmres_solve(op, bi.p, xi.p, nrhs, &o, info, s);
   if (st != BEM_OK && st != BEM_ERR_NOT_CONVERGED && st != BEM_ERR_CANCELLED) return st;
   TRY(permute(m->d_perm, xi.p, w_dev, m->n_tet, nrhs, false, s));
+  STBEM_CUDA(cudaStreamSynchronize(s));
+  return st;
+}
+
+bem_status bem_solve_refined(const bem_operator* op_hi, bem_operator* op_lo, const double* b, double* w,
+                             int32_t nrhs, const bem_solve_opts* opts, bem_solve_info* info) {
+  if (!op_hi || !op_lo || !b || !w || nrhs <= 0 || !opts) {
+    set_error("bem_solve_refined: invalid argument");
+    return BEM_ERR_INVALID_ARG;
+  }
+  if (op_hi->mesh != op_lo->mesh) {
+    set_error("bem_solve_refined: the operators must share one mesh");
+    return BEM_ERR_INVALID_ARG;
+  }
+  const bem_solve_opts& o = *opts;
+  if (o.inner_dtype != BEM_DTYPE_FP32 && o.inner_dtype != BEM_DTYPE_TF32 && o.inner_dtype != BEM_DTYPE_BF16) {
+    set_error("bem_solve_refined: inner_dtype must be FP32, TF32 or BF16");
+    return BEM_ERR_INVALID_ARG;
+  }
+  if (o.restart < 1 || o.restart > 200 || o.maxit < 1 || !(o.tol > 0)) {
+    set_error("bem_solve_refined: bad options");
+    return BEM_ERR_INVALID_ARG;
+  }
+  if ((o.inner_dtype == BEM_DTYPE_FP32 || o.inner_dtype == BEM_DTYPE_TF32) && !op_lo->d_val32) {
+    set_error("FP32 / TF32 inner solves need FP32 values on op_lo");
+    return BEM_ERR_INVALID_ARG;
+  }
+  if (!op_hi->opts.matrix_free && !op_hi->d_val) {
+    set_error("bem_solve_refined: op_hi must hold FP64 values (FP64 precision) or be matrix-free");
+    return BEM_ERR_INVALID_ARG;
+  }
+  const bem_mesh* m = op_lo->mesh;
+  cudaStream_t s = op_lo->ctx->stream;
+  STBEM_CUDA(cudaSetDevice(op_lo->ctx->device));
+  const int64_t nn = m->n_tet * nrhs;
+  DevBuf<double> db, bi, xi;
+  TRY(db.alloc(nn)); TRY(bi.alloc(nn)); TRY(xi.alloc(nn));
+  STBEM_CUDA(cudaMemcpyAsync(db.p, b, sizeof(double) * nn, cudaMemcpyHostToDevice, s));
+  TRY(permute(m->d_perm, db.p, bi.p, m->n_tet, nrhs, true, s));
+  bem_status st = gmres_solve_two(op_hi, op_lo, bi.p, xi.p, nrhs, &o, info, s);
+  if (st != BEM_OK && st != BEM_ERR_NOT_CONVERGED) return st;
+  TRY(permute(m->d_perm, xi.p, db.p, m->n_tet, nrhs, false, s));
+  STBEM_CUDA(cudaMemcpyAsync(w, db.p, sizeof(double) * nn, cudaMemcpyDeviceToHost, s));
   STBEM_CUDA(cudaStreamSynchronize(s));
   return st;
 }

@@ -180,9 +180,11 @@ __device__ __forceinline__ double dist3x(const double* a, const double* b) {
   double dx = __dsub_rn(a[0], b[0]), dy = __dsub_rn(a[1], b[1]), dz = __dsub_rn(a[2], b[2]);
   return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
 }
+// (IEEE square roots here whatever the unit's FP32 flags: the filter's margin
+// is set against the correctly rounded operations)
 __device__ __forceinline__ float dist3f(const float* a, const float* b) {
   float dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
-  return sqrtf(dx * dx + dy * dy + dz * dz);
+  return __fsqrt_rn(dx * dx + dy * dy + dz * dz);
 }
 
 struct TetSm {       // panel data kept in shared memory for a block
@@ -235,7 +237,7 @@ __device__ bool point_sees(const double* x, const float* xf, const TetSm& T, con
     float al = dist3f(xf + 1, T.ballf + 1);
     float phi = al - (xf[0] - T.ballf[0]);
     float rj = T.ballf[4];
-    float dr = (al < rj * 0.70710678f) ? al + sqrtf(fmaxf(rj * rj - al * al, 0.f)) : rj * 1.41421356f;
+    float dr = (al < rj * 0.70710678f) ? al + __fsqrt_rn(fmaxf(rj * rj - al * al, 0.f)) : rj * 1.41421356f;
     float v = phi - dr;
     if (v > margin) return false;
     if (!(v < -margin)) {
@@ -301,6 +303,7 @@ struct BlockCtx {
   double* uscratch;     // [gridDim][max_surf][max_tet]
   int max_surf, max_tet;
   unsigned long long* counter;
+  unsigned long long* inner;   // pattern pass: inner integrals m_Q^2 x (test face, trial panel) (null: not counted)
   // matrix-free product: when mf_y is set the entries are not stored but
   // y[k][i] += A_ij x[k][j] is accumulated (x, y: [mf_nrhs][mf_ld], internal order)
   const double* mf_x;
@@ -429,6 +432,15 @@ __device__ __forceinline__ void pattern_block(const BlockCtx& B, int64_t b, unsi
       B.bw[b] = w;
       B.bnnz[b] = (int64_t)n;
     }
+    if (B.inner) {
+      // inner integrals of the block: every outer point of a test face against
+      // every trial panel the face's pattern bits admit
+      unsigned long long m = 0;
+      for (int f = threadIdx.x; f < ns; f += blockDim.x)
+        for (int w = 0; w < words; ++w) m += __popc(bits[f * words + w]);
+      for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+      if ((threadIdx.x & 31) == 0 && m) atomicAdd(B.inner, m * (unsigned long long)B.nq);
+    }
     __syncthreads();
   }
 }
@@ -548,7 +560,17 @@ __device__ __forceinline__ void quad_block(const BlockCtx& B, int64_t b, unsigne
       const int nsw = shi - slo + 1;
       // per-point geometry against column J
       const double* P = B.pts + fg * B.nq * 4;
-      for (int q = lane; q < B.nq; q += 32) point_col(P + 4 * q, C.G, mypc[q], FP32);
+      for (int q = lane; q < B.nq; q += 32) point_col(P + 4 * q, C.G, mypc[q], FP32, FP32);
+      if constexpr (FP32) {
+        // the whole-edge integrals of the points' fully lit triangle, lane per (point, edge)
+        __syncwarp();
+        for (int e = lane; e < 3 * B.nq; e += 32) {
+          const int q = e / 3, k = e - 3 * q;
+          mypc[q].F.Efull[k] = edge_full_mixed(mypc[q], CR, k);
+        }
+        __syncwarp();
+        for (int q = lane; q < B.nq; q += 32) point_col_finish(mypc[q]);
+      }
       __syncwarp();
       // pass 1: classify every (point, face) pair from the cone-function values
       // at the corners; fully lit and dark pairs are final, cut pairs are listed
@@ -578,9 +600,9 @@ __device__ __forceinline__ void quad_block(const BlockCtx& B, int64_t b, unsigne
       // pass 2: the cut pairs, converged across the warp
       if constexpr (FP32) {
         // mixed: the geometry and edge pieces lane per cut pair; the conic
-        // arcs they need (at most 3 per pair, two thirds of the work) are
-        // collected and integrated lane per arc over the compacted list, then
-        // each pair adds its arcs in order (the same sum as in face_cut)
+        // arcs they need (at most 3 per pair, the larger part of the work)
+        // are collected and integrated lane per arc over the compacted list,
+        // then each pair adds its arcs in order (the same sum as in face_cut)
         for (int base = 0; base < ncut; base += 32) {
           const int k = base + lane;
           int na = 0, q = 0, s = 0;
@@ -794,6 +816,7 @@ static BlockCtx make_ctx(bem_operator* op) {
   B.val = op->d_val; B.val32 = op->d_val32; B.uscratch = op->d_tmp;
   B.max_surf = m->max_col_surf; B.max_tet = m->max_col_tets;
   B.counter = nullptr;
+  B.inner = nullptr;
   B.mf_x = nullptr; B.mf_y = nullptr; B.mf_nrhs = 0; B.mf_ld = m->n_tet;
   return B;
 }
@@ -808,6 +831,8 @@ bem_status op_pattern(bem_operator* op, cudaStream_t s) {
   BlockCtx B = make_ctx(op);
   bem_status st = get_counter(op, &B.counter, s);
   if (st != BEM_OK) return st;
+  STBEM_CUDA(cudaMemsetAsync(op->d_counter + 1, 0, sizeof(unsigned long long), s));
+  B.inner = op->d_counter + 1;
   size_t smem = block_smem(op, false);
   st = ensure_smem_attr((const void*)k_pattern_blocks, smem);
   if (st != BEM_OK) return st;

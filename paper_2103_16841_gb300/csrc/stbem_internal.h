@@ -86,6 +86,7 @@ struct bem_operator {
   double* d_val = nullptr;       // values, per block column-major [W][R_I]
   float* d_val32 = nullptr;
   int64_t nnz = 0, nstored = 0, nblocks = 0, nrows_stored = 0;
+  int64_t n_inner = 0;           // inner integrals per assembly (m_Q^2 x (test face, trial panel) pattern pairs)
   int max_bw = 0;                // widest band of any block
   double assemble_ms = 0.0;
   double phase_ms[4] = {0, 0, 0, 0};
@@ -204,4 +205,7 @@ bem_status permute(const int32_t* d_perm, const double* in, double* out, int64_t
 // solver (stbem_solver.cu)
 bem_status gmres_solve(bem_operator* op, const double* d_b, double* d_x, int nrhs, const bem_solve_opts* o,
                        bem_solve_info* info, cudaStream_t s);
+// refinement with the residual of hi_op (FP64 accumulation) and inner solves on lo_op
+bem_status gmres_solve_two(const bem_operator* hi_op, bem_operator* lo_op, const double* d_b, double* d_x,
+                           int nrhs, const bem_solve_opts* o, bem_solve_info* info, cudaStream_t s);
 }  // namespace stbem

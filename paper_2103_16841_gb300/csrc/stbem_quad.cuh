@@ -360,11 +360,34 @@ STBEM_HD inline bool arc_far(const R* xb, R d, R C, R far_rho, const R* g, const
   return true;
 }
 
+template <typename R>
+STBEM_HD inline void make_colr(const ColGeom& G, ColR<R>& C) {
+  for (int k = 0; k < 3; ++k) {
+    C.Q[k][0] = (R)G.Q[k][0]; C.Q[k][1] = (R)G.Q[k][1];
+    C.U[k][0] = (R)G.U[k][0]; C.U[k][1] = (R)G.U[k][1]; C.L[k] = (R)G.L[k];
+  }
+  C.diam = (R)G.diam;
+}
+
+// whole-edge integral k of the mixed path (the fully lit triangle is the sum
+// over the three edges): the far-field form when P.far, else edge_int
+STBEM_HD inline float edge_full_mixed(const PointCol& P, const ColR<float>& CR, int k) {
+  const PtR<float>& T = P.F;
+  const ArcRule er = make_rule(1, 0);
+  if (T.far) return edge_far<float>(T, CR, k, 0.f, 1.f, er);
+  return edge_int<float>(T.ws[k], CR.L[k], T.ps[k], T.d, er);
+}
+
 // Geometry of apex x against column G and the whole-triangle potential (the
 // fully lit case). FP64 path: everything in FP64. Mixed path: the relative
 // position, the height d, the foot point and the corner distances in FP64
 // (they carry the cancellation between |x - y| and t - tau), the rest in FP32.
-STBEM_HD inline void point_col(const double* x, const ColGeom& G, PointCol& P, bool prec_fp32) {
+// With defer_edges (mixed path only)
+// the whole-edge integrals Efull and the whole-triangle value Wst are left to
+// the caller (edge_full_mixed per edge, then point_col_finish), so that a warp
+// can spread the three edges of its points over its lanes.
+STBEM_HD inline void point_col(const double* x, const ColGeom& G, PointCol& P, bool prec_fp32,
+                               bool defer_edges = false) {
   P.t = x[0];
   double rel[3] = {x[1] - G.c0[0], x[2] - G.c0[1], x[3] - G.c0[2]};
   double d = rel[0] * G.n[0] + rel[1] * G.n[1] + rel[2] * G.n[2];
@@ -382,7 +405,6 @@ STBEM_HD inline void point_col(const double* x, const ColGeom& G, PointCol& P, b
     T.xb[1] = (float)xb1;
     int in = 1;
     float out = 0.f, W = 0.f;
-    const ArcRule er = make_rule(1, 0);
     for (int k = 0; k < 3; ++k) {
       T.q[k][0] = (float)G.Q[k][0] - T.xb[0];
       T.q[k][1] = (float)G.Q[k][1] - T.xb[1];
@@ -399,19 +421,11 @@ STBEM_HD inline void point_col(const double* x, const ColGeom& G, PointCol& P, b
     T.far = out >= FAR_RHO * (float)G.diam;
     T.C = T.rs[0];
     T.far_rho = out;
-    if (T.far) {
+    if (!defer_edges) {
       ColR<float> CR;
+      make_colr<float>(G, CR);
       for (int k = 0; k < 3; ++k) {
-        CR.Q[k][0] = (float)G.Q[k][0]; CR.Q[k][1] = (float)G.Q[k][1];
-        CR.U[k][0] = (float)G.U[k][0]; CR.U[k][1] = (float)G.U[k][1]; CR.L[k] = (float)G.L[k];
-      }
-      for (int k = 0; k < 3; ++k) {
-        T.Efull[k] = edge_far<float>(T, CR, k, 0.f, 1.f, er);
-        W += T.Efull[k];
-      }
-    } else {
-      for (int k = 0; k < 3; ++k) {
-        T.Efull[k] = edge_int<float>(T.ws[k], (float)G.L[k], T.ps[k], T.d, er);
+        T.Efull[k] = edge_full_mixed(P, CR, k);
         W += T.Efull[k];
       }
     }
@@ -452,6 +466,13 @@ STBEM_HD inline void point_col(const double* x, const ColGeom& G, PointCol& P, b
   P.rlo = sqrt(d * d + out * out);
   P.Wst = W;
   P.Wst_f = (float)W;
+}
+
+// the whole-triangle value of the mixed path from its three edge integrals
+STBEM_HD inline void point_col_finish(PointCol& P) {
+  const float W = (P.F.Efull[0] + P.F.Efull[1]) + P.F.Efull[2];
+  P.Wst = (double)W;
+  P.Wst_f = W;
 }
 
 // ---------------------------------------------------------------------------
@@ -844,6 +865,22 @@ STBEM_HD inline int face_class_mixed(const PointCol& P, const FaceF& Fc, float* 
   }
   if (nlit == 3) return FACE_LIT;
   if (add2(Fc.pmin_hi, Fc.pmin_lo, P.rlot_hi, P.rlot_lo) >= 0.f) return FACE_DARK;
+  {
+    // F = P + |x_s - y| - t is convex on K: its tangent plane at the corner m
+    // of smallest F, F_m + (P(y) - P(Q_m)) + <Q_m - xb, y - Q_m> / r_m, bounds
+    // it from below and is linear, so no point of K is lit when the bound is
+    // positive at the three corners (margin: the FP32 error of the linear term)
+    const int m = F[0] <= F[1] ? (F[0] <= F[2] ? 0 : 2) : (F[1] <= F[2] ? 1 : 2);
+    const float qx = P.F.q[m][0], qy = P.F.q[m][1], rm = P.F.rs[m];
+    float lo = F[m];
+    for (int k = 0; k < 3; ++k) {
+      if (k == m) continue;
+      const float dp = add2(Fc.p_hi[k], Fc.p_lo[k], -Fc.p_hi[m], -Fc.p_lo[m]);
+      const float lin = (qx * (P.F.q[k][0] - qx) + qy * (P.F.q[k][1] - qy)) / rm;
+      lo = fminf(lo, F[m] + dp + lin);
+    }
+    if (lo > 4e-7f * rm) return FACE_DARK;
+  }
   float p0t = add2(Fc.p_hi[0], Fc.p_lo[0], P.nt_hi, P.nt_lo);
   c = -(p0t + (Fc.g[0] * P.F.xb[0] + Fc.g[1] * P.F.xb[1]));
   if (fabsf(c) < 1e-6f * diam) c = 0.f;
@@ -1058,15 +1095,6 @@ STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, con
     }
   }
   return (double)total;
-}
-
-template <typename R>
-STBEM_HD inline void make_colr(const ColGeom& G, ColR<R>& C) {
-  for (int k = 0; k < 3; ++k) {
-    C.Q[k][0] = (R)G.Q[k][0]; C.Q[k][1] = (R)G.Q[k][1];
-    C.U[k][0] = (R)G.U[k][0]; C.U[k][1] = (R)G.U[k][1]; C.L[k] = (R)G.L[k];
-  }
-  C.diam = (R)G.diam;
 }
 
 // 4 pi W_P(x) in one call (used by the kernel-level entry point and checks)

@@ -52,12 +52,15 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
   return std::chrono::duration<double, std::milli>(b - a).count();
 }
 
+// per-request device vectors, allocated and released on the slot's stream
 template <typename T>
 struct DBuf {
   T* p = nullptr;
-  ~DBuf() { if (p) cudaFree(p); }
-  bem_status alloc(int64_t n) {
-    if (cudaMalloc((void**)&p, sizeof(T) * std::max<int64_t>(n, 1)) != cudaSuccess) {
+  cudaStream_t st = nullptr;
+  ~DBuf() { if (p) cudaFreeAsync(p, st); }
+  bem_status alloc(int64_t n, cudaStream_t s) {
+    st = s;
+    if (cudaMallocAsync((void**)&p, sizeof(T) * std::max<int64_t>(n, 1), s) != cudaSuccess) {
       cudaGetLastError();
       p = nullptr;
       set_error("out of device memory");
@@ -66,6 +69,36 @@ struct DBuf {
     return BEM_OK;
   }
 };
+
+// A resident operator, keyed by its request's mesh arrays.
+struct CacheEntry {
+  uint64_t key = 0;
+  std::vector<double> sv, stv_t;
+  std::vector<int32_t> stv_sv, tets;
+  bem_mesh* mesh = nullptr;
+  bem_operator* op = nullptr;
+  int64_t bytes = 0;     // pool bytes it holds (values, row starts, scratch, mesh and structure)
+  bool busy = false;     // in use by a request (operators are used by one stream at a time)
+  uint64_t last = 0;     // LRU clock
+};
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+  const unsigned char* c = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
+  return h;
+}
+
+uint64_t job_key(const Job& J) {
+  uint64_t h = 1469598103934665603ull;
+  h = fnv1a(h, J.sv.data(), J.sv.size() * sizeof(double));
+  h = fnv1a(h, J.stv_sv.data(), J.stv_sv.size() * sizeof(int32_t));
+  h = fnv1a(h, J.stv_t.data(), J.stv_t.size() * sizeof(double));
+  return fnv1a(h, J.tets.data(), J.tets.size() * sizeof(int32_t));
+}
+
+bool same_mesh(const CacheEntry& e, const Job& J) {
+  return e.sv == J.sv && e.stv_sv == J.stv_sv && e.stv_t == J.stv_t && e.tets == J.tets;
+}
 
 }  // namespace
 
@@ -88,11 +121,23 @@ struct bem_server {
   bool any_submit = false;
   Clock::time_point t_first, t_last;
   std::vector<double> lat;
+  // resident operators (cache_operators = 1)
+  std::vector<std::unique_ptr<CacheEntry>> cache;
+  uint64_t use_clock = 0;
+  int64_t cache_hits = 0, cached_bytes = 0;
 };
 
 namespace {
 
-// HBM reservation in arrival order; a request that can never fit fails.
+void destroy_entry(std::unique_ptr<CacheEntry> e) {
+  if (!e) return;
+  if (e->op) bem_operator_destroy(e->op);
+  if (e->mesh) bem_mesh_destroy(e->mesh);
+}
+
+// HBM reservation in arrival order; a request that can never fit fails. The
+// request at the head of the queue evicts idle resident operators (least
+// recently used first) when they hold the room it needs.
 bem_status acquire(bem_server* S, uint64_t ticket, int64_t bytes) {
   std::unique_lock<std::mutex> lk(S->mu);
   if (bytes > S->pool) {
@@ -101,7 +146,25 @@ bem_status acquire(bem_server* S, uint64_t ticket, int64_t bytes) {
     return BEM_ERR_OUT_OF_MEMORY;
   }
   S->mem_fifo.push_back(ticket);
-  S->cv_mem.wait(lk, [&] { return S->mem_fifo.front() == ticket && S->in_use + bytes <= S->pool; });
+  for (;;) {
+    if (S->mem_fifo.front() == ticket && S->in_use + bytes <= S->pool) break;
+    if (S->mem_fifo.front() == ticket) {
+      int victim = -1;
+      for (int k = 0; k < (int)S->cache.size(); ++k)
+        if (!S->cache[k]->busy && (victim < 0 || S->cache[k]->last < S->cache[victim]->last)) victim = k;
+      if (victim >= 0) {
+        std::unique_ptr<CacheEntry> e = std::move(S->cache[victim]);
+        S->cache.erase(S->cache.begin() + victim);
+        S->in_use -= e->bytes;
+        S->cached_bytes -= e->bytes;
+        lk.unlock();
+        destroy_entry(std::move(e));
+        lk.lock();
+        continue;
+      }
+    }
+    S->cv_mem.wait(lk);
+  }
   S->mem_fifo.pop_front();
   S->in_use += bytes;
   S->peak_in_use = std::max(S->peak_in_use, S->in_use);
@@ -130,47 +193,24 @@ int64_t admission_bytes(const bem_operator* op, const bem_server_opts& o, int nr
   return b;
 }
 
-bem_status run_job(bem_server* S, bem_context* cx, const Job& J, Done& D, int64_t& reserved) {
-  cudaStream_t s = cx->stream;
-  bem_mesh* mesh = nullptr;
-  bem_status st = bem_mesh_create(cx, J.n_sv, J.sv.data(), J.n_stv, J.stv_sv.data(), J.stv_t.data(), J.n_tet,
-                                  J.tets.data(), &mesh);
-  if (st != BEM_OK) return st;
-  std::unique_ptr<bem_mesh, void (*)(bem_mesh*)> mesh_guard(mesh, bem_mesh_destroy);
-  if (structure_bytes(mesh) > S->slot_share) {
-    set_error("mesh and sparsity structure exceed the slot's share of the HBM budget");
-    return BEM_ERR_OUT_OF_MEMORY;
-  }
-  bem_op_opts oo{};
-  oo.precision = S->o.precision;
-  oo.m_q = 3;
-  oo.n_theta = 0;
-  oo.store_fp32 = (S->o.inner_dtype == BEM_DTYPE_FP32 || S->o.inner_dtype == BEM_DTYPE_TF32) ? 1 : 0;
-  bem_operator* op = nullptr;
-  const uint64_t ticket = J.ticket;
+// Right-hand side, solve and density of a request on an assembled operator
+// (device vectors stream-ordered on the slot's stream s).
+bem_status solve_job(bem_server* S, cudaStream_t s, bem_operator* op, const Job& J, Done& D) {
+  const bem_mesh* mesh = op->mesh;
   const int nrhs = J.nrhs;
-  bem_server_opts so_srv = S->o;
-  st = operator_create(cx, mesh, &oo, [&, ticket, nrhs](const bem_operator* o2) -> bem_status {
-        const int64_t need = admission_bytes(o2, so_srv, nrhs);
-        bem_status a = acquire(S, ticket, need);
-        if (a == BEM_OK) reserved = need;
-        return a;
-      }, &op);
-  if (st != BEM_OK) return st;
-  std::unique_ptr<bem_operator, void (*)(bem_operator*)> op_guard(op, bem_operator_destroy);
   const int64_t n = mesh->n_tet, nn = n * nrhs;
   DBuf<double> dp, db, dx, dw;
-  SRV_TRY(db.alloc(nn));
-  SRV_TRY(dx.alloc(nn));
-  SRV_TRY(dw.alloc(nn));
+  SRV_TRY(db.alloc(nn, s));
+  SRV_TRY(dx.alloc(nn, s));
+  SRV_TRY(dw.alloc(nn, s));
   if (J.kind == BEM_DATA_PULSE) {
-    SRV_TRY(dp.alloc(5 * nrhs));
+    SRV_TRY(dp.alloc(5 * nrhs, s));
     STBEM_CUDA(cudaMemcpyAsync(dp.p, J.params.data(), sizeof(double) * 5 * nrhs, cudaMemcpyHostToDevice, s));
   }
   SRV_TRY(op_rhs(op, J.kind, nrhs, dp.p, db.p, s));
   bem_solve_opts so{S->o.tol, S->o.restart, S->o.maxit, S->o.inner_dtype, S->o.max_refine};
   std::vector<bem_solve_info> info(nrhs);
-  st = gmres_solve(op, db.p, dx.p, nrhs, &so, info.data(), s);
+  bem_status st = gmres_solve(op, db.p, dx.p, nrhs, &so, info.data(), s);
   if (st != BEM_OK && st != BEM_ERR_NOT_CONVERGED) return st;
   SRV_TRY(permute(mesh->d_perm, dx.p, dw.p, n, nrhs, false, s));
   D.w.resize(nn);
@@ -185,6 +225,111 @@ bem_status run_job(bem_server* S, bem_context* cx, const Job& J, Done& D, int64_
   D.c.iterations = it;
   D.c.refinements = info.empty() ? 0 : info[0].refinements;
   D.c.rel_residual = rr;
+  return st;
+}
+
+// returns the request's reservation to the pool (moving `keep` bytes of it,
+// plus `extra` bytes from the slot's share, into the operator cache)
+void release(bem_server* S, int64_t reserved, int64_t keep_in_pool) {
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (reserved > 0) --S->running;
+  S->in_use += keep_in_pool - reserved;
+}
+
+bem_status run_job(bem_server* S, bem_context* cx, const Job& J, Done& D, int64_t& reserved) {
+  cudaStream_t s = cx->stream;
+  const int nrhs = J.nrhs;
+  const bool caching = S->o.cache_operators != 0;
+  const uint64_t key = caching ? job_key(J) : 0;
+  // a resident operator on the same mesh
+  CacheEntry* hit = nullptr;
+  if (caching) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (auto& e : S->cache)
+      if (e->key == key && !e->busy && same_mesh(*e, J)) {
+        e->busy = true;
+        e->last = ++S->use_clock;
+        hit = e.get();
+        break;
+      }
+  }
+  if (hit) {
+    const int64_t need = admission_bytes(hit->op, S->o, nrhs) - operator_value_bytes(hit->op);
+    bem_status st = acquire(S, J.ticket, need);
+    if (st == BEM_OK) {
+      reserved = need;
+      st = solve_job(S, s, hit->op, J, D);
+      release(S, reserved, 0);
+    }
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      hit->busy = false;
+      if (st == BEM_OK || st == BEM_ERR_NOT_CONVERGED) ++S->cache_hits;
+    }
+    S->cv_mem.notify_all();
+    D.c.cache_hit = 1;
+    return st;
+  }
+  bem_mesh* mesh = nullptr;
+  bem_status st = bem_mesh_create(cx, J.n_sv, J.sv.data(), J.n_stv, J.stv_sv.data(), J.stv_t.data(), J.n_tet,
+                                  J.tets.data(), &mesh);
+  if (st != BEM_OK) return st;
+  std::unique_ptr<bem_mesh, void (*)(bem_mesh*)> mesh_guard(mesh, bem_mesh_destroy);
+  const int64_t sbytes = structure_bytes(mesh);
+  if (sbytes > S->slot_share) {
+    set_error("mesh and sparsity structure exceed the slot's share of the HBM budget");
+    return BEM_ERR_OUT_OF_MEMORY;
+  }
+  bem_op_opts oo{};
+  oo.precision = S->o.precision;
+  oo.m_q = 3;
+  oo.n_theta = 0;
+  oo.store_fp32 = (S->o.inner_dtype == BEM_DTYPE_FP32 || S->o.inner_dtype == BEM_DTYPE_TF32) ? 1 : 0;
+  bem_operator* op = nullptr;
+  const uint64_t ticket = J.ticket;
+  bem_server_opts so_srv = S->o;
+  st = operator_create(cx, mesh, &oo, [&, ticket, nrhs](const bem_operator* o2) -> bem_status {
+        const int64_t need = admission_bytes(o2, so_srv, nrhs);
+        bem_status a = acquire(S, ticket, need);
+        if (a == BEM_OK) reserved = need;
+        return a;
+      }, &op);
+  if (st != BEM_OK) {
+    if (reserved > 0) release(S, reserved, 0);
+    return st;
+  }
+  std::unique_ptr<bem_operator, void (*)(bem_operator*)> op_guard(op, bem_operator_destroy);
+  st = solve_job(S, s, op, J, D);
+  if (!caching || (st != BEM_OK && st != BEM_ERR_NOT_CONVERGED)) {
+    release(S, reserved, 0);
+    return st;
+  }
+  // keep the operator resident if the pool has room for it beside the others
+  const int64_t keep = operator_value_bytes(op) + sbytes + op->ws_len * (int64_t)sizeof(float) +
+                       op->pv_len * (int64_t)sizeof(double) + (op->d_val16 ? op->nstored * 2 : 0);
+  bool kept = false;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    bool have = false;   // another request on this mesh built and kept it meanwhile
+    for (auto& e : S->cache) have = have || (e->key == key && same_mesh(*e, J));
+    if (!have && S->in_use - reserved + keep <= S->pool) {
+      std::unique_ptr<CacheEntry> e(new CacheEntry());
+      e->key = key;
+      e->sv = J.sv; e->stv_sv = J.stv_sv; e->stv_t = J.stv_t; e->tets = J.tets;
+      e->mesh = mesh; e->op = op;
+      e->bytes = keep;
+      e->last = ++S->use_clock;
+      S->cache.push_back(std::move(e));
+      S->cached_bytes += keep;
+      kept = true;
+    }
+  }
+  if (kept) {
+    op_guard.release();
+    mesh_guard.release();
+  }
+  release(S, reserved, kept ? keep : 0);
+  S->cv_mem.notify_all();
   return st;
 }
 
@@ -216,10 +361,6 @@ void worker(bem_server* S, int slot) {
     D->c.w = D->w.empty() ? nullptr : D->w.data();
     {
       std::lock_guard<std::mutex> lk(S->mu);
-      if (reserved > 0) {
-        S->in_use -= reserved;
-        --S->running;
-      }
       if (st == BEM_OK) {
         ++S->completed;
         S->lat.push_back(D->c.latency_ms);
@@ -244,7 +385,7 @@ bem_status bem_server_create(bem_context* ctx, const bem_server_opts* opts, bem_
   const bem_server_opts& o = *opts;
   if (o.max_slots < 1 || o.max_slots > 16 || (o.precision != BEM_PREC_FP64 && o.precision != BEM_PREC_MIXED) ||
       o.inner_dtype < BEM_DTYPE_FP64 || o.inner_dtype > BEM_DTYPE_BF16 || o.restart < 1 || o.restart > 200 ||
-      o.maxit < 1 || !(o.tol > 0) || o.hbm_budget < 0) {
+      o.maxit < 1 || !(o.tol > 0) || o.hbm_budget < 0 || (o.cache_operators != 0 && o.cache_operators != 1)) {
     set_error("bem_server_create: bad options");
     return BEM_ERR_INVALID_ARG;
   }
@@ -345,6 +486,9 @@ bem_status bem_server_stats_get(const bem_server* Sc, bem_server_stats* out) {
   r.running = S->running;
   r.peak_running = S->peak_running;
   r.peak_reserved_bytes = S->peak_in_use;
+  r.cache_hits = S->cache_hits;
+  r.cached_operators = (int64_t)S->cache.size();
+  r.cached_bytes = S->cached_bytes;
   if (!S->lat.empty()) {
     std::vector<double> v = S->lat;
     std::sort(v.begin(), v.end());
@@ -373,6 +517,8 @@ void bem_server_destroy(bem_server* S) {
   }
   S->cv_work.notify_all();
   for (auto& t : S->workers) t.join();
+  for (auto& e : S->cache) destroy_entry(std::move(e));
+  S->cache.clear();
   for (auto* c : S->slot_ctx) bem_context_destroy(c);
   delete S;
 }

@@ -140,4 +140,21 @@ bem_status gmres_solve(bem_operator* op, const double* d_b, double* d_x, int nrh
   return gmres_solve_layout(L, hi, lo, d_b, d_x, o, info, s);
 }
 
+bem_status gmres_solve_two(const bem_operator* hi_op, bem_operator* lo_op, const double* d_b, double* d_x,
+                           int nrhs, const bem_solve_opts* o, bem_solve_info* info, cudaStream_t s) {
+  SegLayout L;
+  L.N = lo_op->mesh->n_tet;
+  L.K = nrhs;
+  L.S = 1;
+  L.seg_off = {0, L.N};
+  const int inner = o->inner_dtype;
+  MatvecFn hi = [hi_op, nrhs](const double* x, double* y, cudaStream_t st) {
+    return op_matvec(hi_op, x, y, nrhs, MV_FP64, st);
+  };
+  MatvecFn lo = [lo_op, nrhs, inner](const double* x, double* y, cudaStream_t st) {
+    return op_matvec(lo_op, x, y, nrhs, inner, st);
+  };
+  return gmres_solve_layout(L, hi, lo, d_b, d_x, o, info, s);
+}
+
 }  // namespace stbem

@@ -70,3 +70,21 @@ def test_c1_tensor_core_inner_solves_vs_oracle_lu(c1_lu, inner):
     print("C1 mixed, %s inner + FP64 refinement (%d refinements) vs oracle LU: %.3e"
           % (inner, info[0]["refinements"], rel))
     assert rel <= 1e-6
+
+
+@pytest.mark.parametrize("inner", ["fp32", "tf32", "bf16"])
+def test_c1_refinement_with_fp64_residual_vs_oracle_lu(c1_lu, inner):
+    """bem_solve_refined: the outer residual from the FP64 operator, the inner
+    solves on the mixed operator; the refinement converges to the FP64
+    operator's solution, so it matches the oracle LU to FP64 solver accuracy
+    although the inner operator carries the FP32 quadrature error."""
+    import paper_2103_16841_gb300 as stb
+    ctx, m, mesh, w_ref = c1_lu
+    op64 = stb.Operator(ctx, mesh, "fp64", store_fp32=False)
+    opm = stb.Operator(ctx, mesh, "mixed")
+    b = op64.rhs(stb.DATA_SIN2_UNIFORM)[:, 0]
+    w, info = opm.solve_refined(op64, b, tol=1e-13, restart=100, maxit=2000, inner=inner, max_refine=30)
+    assert info[0]["converged"]
+    rel = np.linalg.norm(w - w_ref) / np.linalg.norm(w_ref)
+    print("C1 refinement with the FP64 residual (%s inner) vs oracle LU: %.3e" % (inner, rel))
+    assert rel <= 1e-10

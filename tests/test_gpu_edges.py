@@ -165,4 +165,6 @@ def test_cone_grazing_a_corner_of_timelike_faces(ctx):
         cols = o64.pattern_rows(rows)
         ij = np.array([(r, c) for r, cs in zip(rows, cols) for c in cs], dtype=np.int32)
         a64, am = o64.entries(ij), om.entries(ij)
-        assert np.abs(am - a64).max() <= 4e-6 * np.abs(a64).max()
+        err = np.abs(am - a64).max() / np.abs(a64).max()
+        print("grazing ellipsoid %d: mixed vs FP64 entries, normwise %.3e" % (k, err))
+        assert err <= 1e-6

@@ -64,10 +64,12 @@ def test_c2_mixed_values_finite(c2_mixed):
 
 def test_c2_mixed_pattern_rows_and_entries(c2_mixed):
     m, mesh, op = c2_mixed
-    # FP32 quadrature far from the apex: the contour terms of Green's formula are
-    # O(diam K) while W is O(diam K^2 / dist); with dist / diam K up to ~30 on
-    # this mesh the normwise error reaches ~40 FP32 ulps (measured 1.8e-6..2.5e-6)
-    _row_check(op, m, 6, 4e-6, seed=21)
+    # entries of the mixed operator against the FP64 oracle, normwise: the
+    # far-field contour form keeps FP32 pieces at relative accuracy eps; the
+    # largest remaining errors are on faces that the cone only just reaches
+    # (a lit ellipse much smaller than K), measured 5.3e-7 against the FP64
+    # operator over 102,907 entries of 12 rows
+    _row_check(op, m, 6, 1e-6, seed=21)
 
 
 def test_c2_mixed_solve_converges(c2_mixed):
@@ -77,6 +79,40 @@ def test_c2_mixed_solve_converges(c2_mixed):
     w, info = op.solve(b, tol=1e-8, restart=50, maxit=400, inner="fp32", max_refine=8)
     assert info[0]["converged"] and info[0]["rel_residual"] <= 1e-8
     assert np.isfinite(w).all()
+
+
+def test_c2_mixed_solutions_vs_fp64_operator(ctx, c2_mixed):
+    """The reduced-precision form at the benchmark size (122,880 panels):
+    solutions of the mixed operator (FP32 quadrature values; FP32, TF32 and
+    BF16 inner GMRES with FP64 refinement) against the FP64 operator's
+    solutions of the same mesh and data: <= 1e-6 relative per right-hand side.
+    With the FP64 operator as the refinement's residual operator the mixed
+    inner solves reach the FP64 solution itself."""
+    import paper_2103_16841_gb300 as stb
+    m, mesh, op = c2_mixed
+    op64 = stb.Operator(ctx, mesh, "fp64", store_fp32=False)
+    rel = lambda w, w64: np.linalg.norm(w - w64, axis=0) / np.linalg.norm(w64, axis=0)
+    b = op.rhs(stb.DATA_PULSE, inputs.pulse_params(1, seed=2, fixed_c=1.5))
+    w64, i64 = op64.solve(b, tol=1e-12, restart=100, maxit=4000)
+    assert i64[0]["converged"]
+    wm, im = op.solve(b, tol=1e-10, restart=50, maxit=600, inner="fp32", max_refine=12)
+    assert im[0]["converged"]
+    e1 = rel(wm, w64)
+    B = op.rhs(stb.DATA_PULSE, inputs.pulse_params(64, seed=2)[:4])
+    W64, iw = op64.solve(B, tol=1e-11, restart=100, maxit=4000)
+    assert all(i["converged"] for i in iw)
+    errs = {"fp32 (1 pulse)": e1}
+    for inner in ("tf32", "bf16"):
+        Wm, info = op.solve(B, tol=1e-10, restart=50, maxit=600, inner=inner, max_refine=30)
+        assert all(i["converged"] for i in info)
+        errs[inner] = rel(Wm, W64)
+    Wr, ir = op.solve_refined(op64, B, tol=1e-11, restart=50, maxit=600, inner="tf32", max_refine=30)
+    assert all(i["converged"] for i in ir)
+    print("C2 mixed vs FP64 operator per RHS:", errs, "refined with the FP64 residual:", rel(Wr, W64))
+    for v in errs.values():
+        assert v.max() <= 1e-6, errs
+    assert rel(Wr, W64).max() <= 1e-9
+    op64.close()
 
 
 def test_l3x16_fp64_pattern_rows_and_entries(ctx):
@@ -103,7 +139,7 @@ def test_mixed_solution_matches_fp64(ctx):
     rel = np.linalg.norm(wm - w64, axis=0) / np.linalg.norm(w64, axis=0)
     print("mixed vs FP64 solution per RHS:", rel)
     assert all(i["converged"] for i in info)
-    assert rel.max() <= 1e-5, rel
+    assert rel.max() <= 1e-6, rel
 
 
 def _l2_error(m, w):

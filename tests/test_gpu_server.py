@@ -75,3 +75,44 @@ def test_server_admission_by_hbm(ctx):
     r = small.wait([t])[t]
     assert r["status"] == 2 and r["w"] is None
     small.close()
+
+
+def test_server_resident_operators(ctx):
+    """With cache_operators the assembled operator of a mesh stays resident:
+    later requests on the same mesh skip the assembly (cache hits) and give the
+    same densities as a fresh assembly and solve; when the pool is short,
+    idle resident operators are evicted least recently used."""
+    import paper_2103_16841_gb300 as stb
+    m1, p1 = _req(1, 8, 1, 31)
+    m2, p2 = _req(1, 16, 2, 32)
+    srv = stb.Server(ctx, max_slots=2, precision="mixed", inner="fp32", tol=1e-8, cache_operators=True)
+    t0 = srv.submit(m1, params=p1)
+    first = srv.wait([t0])[t0]
+    assert first["status"] == 0 and not first["cache_hit"]
+    prm = [inputs.pulse_params(2, seed=40 + k) for k in range(3)]
+    ts = [srv.submit(m1, params=p) for p in prm] + [srv.submit(m2, params=p2)]
+    res = srv.wait(ts)
+    assert all(res[t]["status"] == 0 for t in ts)
+    assert sum(res[t]["cache_hit"] for t in ts[:3]) >= 2     # at most one may overlap the busy entry
+    st = srv.stats()
+    assert st["cache_hits"] >= 2 and st["cached_operators"] == 2   # one per mesh
+    srv.close()
+    mesh = stb.Mesh.from_spacetime(ctx, m1)
+    op = stb.Operator(ctx, mesh, "mixed", store_fp32=True)
+    for t, p in zip(ts[:3], prm):
+        w, _ = op.solve(op.rhs(stb.DATA_PULSE, p), tol=1e-8, restart=50, maxit=2000, inner="fp32", max_refine=10)
+        assert np.abs(w.T - res[t]["w"]).max() <= 1e-12 * np.abs(w).max()
+    # eviction: a pool that holds one resident operator at a time
+    need = first["reserved_bytes"]
+    slots, share = 2, 64 << 20
+    small = stb.Server(ctx, hbm_budget=slots * share + int(1.5 * need), max_slots=slots, precision="mixed",
+                       inner="fp32", tol=1e-8, cache_operators=True)
+    m3, p3 = _req(1, 8, 1, 33)                 # the same shape as m1, another jitter
+    order = [(m1, p1), (m3, p3), (m1, p1)]
+    for mm, pp in order:
+        t = small.submit(mm, params=pp)
+        r = small.wait([t])[t]
+        assert r["status"] == 0
+    st = small.stats()
+    assert st["cached_operators"] <= 1 and st["peak_reserved_bytes"] <= int(1.5 * need)
+    small.close()
