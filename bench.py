@@ -575,7 +575,7 @@ def main():
                     help="right-hand sides of the multi-RHS leg (0: skip)")
     ap.add_argument("--batch", type=int, default=64,
                     help="small scatterers of the batch leg (0: skip; 512 is the full batch)")
-    ap.add_argument("--serve-requests", dest="serve_requests", type=int, default=24,
+    ap.add_argument("--serve-requests", dest="serve_requests", type=int, default=16,
                     help="requests of the serving leg (0: skip)")
     ap.add_argument("--serve-rate", dest="serve_rate", type=float, default=1.0, help="Poisson arrivals per second")
     ap.add_argument("--serve-slots", dest="serve_slots", type=int, default=4)

@@ -327,6 +327,9 @@ STBEM_HD inline bool arc_far(const R* xb, R d, R C, R far_rho, const R* g, const
   const R qAx = q0x + uA[0], qAy = q0y + uA[1];
   const R rA = sqrt(qAx * qAx + qAy * qAy + d * d);
   const R mx = qAx + rA * g[0], my = qAy + rA * g[1];
+  // m cancels where the conic bends sharply at A (|grad P| near 1, or the cone
+  // just reaching the plane); its FP32 rounding then sets the arc's shape
+  if (!(mx * mx + my * my >= R(0.0025) * (qAx * qAx + qAy * qAy))) return false;
   const R gD = g[0] * Dx + g[1] * Dy, gn = g[0] * nx + g[1] * ny;
   const R QD = l2 - gD * gD, a = R(1) - gn * gn, BDn = -gD * gn;
   const R b0 = R(2) * (mx * nx + my * ny), b1 = b0 + R(2) * BDn;
@@ -485,12 +488,14 @@ struct ArcFrame {
   R c, d, g[2];
 };
 
+// D0 = c^2 - d^2 (1 - |g|^2) is passed in: it sets the conic's size and
+// cancels when the cone only just reaches the face plane, so callers form it
+// with more care than c and d allow (see cut_in_mixed).
 template <typename R>
-STBEM_HD inline bool arc_frame(R c, R d, const R* g, ArcFrame<R>& F) {
+STBEM_HD inline bool arc_frame(R c, R d, const R* g, R D0, ArcFrame<R>& F) {
   R w[3] = {d * g[0], d * g[1], c};
   R wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
   if (!(wn > R(0))) return false;
-  R D0 = c * c - d * d * (R(1) - (g[0] * g[0] + g[1] * g[1]));
   if (!(D0 > R(0))) return false;
   for (int i = 0; i < 3; ++i) F.wh[i] = w[i] / wn;
   F.ca = d / wn;
@@ -727,8 +732,8 @@ STBEM_HD __noinline__ R arc_d0(const R* A, const R* dAB, bool full, R c, const R
 // left; full = closed ellipse (A, dAB ignored). dAB is passed on its own so
 // that short arcs far from xb keep their relative accuracy.
 template <typename R>
-STBEM_HD __noinline__ R conic_arc(const R* A, const R* dAB, bool full, R c, R d, const R* g, const ArcRule& rule,
-                                  double c64, const double* g64, bool tiny_is_short = false) {
+STBEM_HD __noinline__ R conic_arc(const R* A, const R* dAB, bool full, R c, R d, const R* g, R D0,
+                                  const ArcRule& rule, double c64, const double* g64, bool tiny_is_short = false) {
   if (d == R(0)) {
     // closed form in FP64 in every precision: it is a difference of
     // antiderivative values, and it only arises for coplanar pairs
@@ -737,7 +742,7 @@ STBEM_HD __noinline__ R conic_arc(const R* A, const R* dAB, bool full, R c, R d,
     return (R)arc_d0<double>(A64, D64, full, c64, g64);
   }
   ArcFrame<R> F;
-  if (!arc_frame<R>(c, d, g, F)) return R(0);
+  if (!arc_frame<R>(c, d, g, D0, F)) return R(0);
   if (F.sa < R(sizeof(R) == 4 ? 1e-6 : 1e-14)) return R(0);
   const R pi = (R)STBEM_PI, twopi = (R)(2.0 * STBEM_PI);
   R thA = full ? R(0) : arc_theta<R>(F, A);
@@ -887,12 +892,13 @@ STBEM_HD inline int face_class_mixed(const PointCol& P, const FaceF& Fc, float* 
   return FACE_CUT;
 }
 
-// Near-singular faces of the mixed path: the apex lies nearly in the plane
-// of K and the cone's vertex nearly on it (|c|, |d| < 0.03 diam K), so the
-// conic passes close to the foot point, where FP32 arcs lose accuracy; the
-// mixed path computes these faces in FP64.
+// Near-singular faces of the mixed path, computed in FP64: the apex lies
+// nearly in the plane of K (|d| < 0.01 diam K: the cone's directions to the
+// plane are nearly tangent to it), or nearly in it with the cone's vertex
+// near the plane as well (|c|, |d| < 0.05 diam K: the conic passes close to
+// its focus). FP32 arcs lose up to 1e-4 of W on both.
 STBEM_HD inline bool near_singular_mixed(float c, float d, float diam) {
-  return fmaxf(fabsf(c), fabsf(d)) < 0.03f * diam;
+  return fabsf(d) < 0.01f * diam || fmaxf(fabsf(c), fabsf(d)) < 0.05f * diam;
 }
 
 // Inputs of the cut case in precision R: cone-function values F_k at the
@@ -901,6 +907,7 @@ STBEM_HD inline bool near_singular_mixed(float c, float d, float diam) {
 template <typename R>
 struct FaceCutIn {
   R F[3], a0[3], a1[3], g[2], c;
+  R D0;                // c^2 - d^2 (1 - |g|^2), the conic's size (see cut_in_mixed)
   double c64, g64[2];
 };
 
@@ -914,6 +921,7 @@ STBEM_HD inline void cut_in_fp64(const PointCol& P, const FaceGeom& Fc, const do
   o.g[0] = o.g64[0] = Fc.g[0];
   o.g[1] = o.g64[1] = Fc.g[1];
   o.c = o.c64 = c;
+  o.D0 = c * c - P.D.d * P.D.d * (1.0 - (Fc.g[0] * Fc.g[0] + Fc.g[1] * Fc.g[1]));
 }
 
 STBEM_HD inline void cut_in_mixed(const PointCol& P, const FaceF& Fc, const float* F, float c, const FaceGeom& F64,
@@ -928,6 +936,19 @@ STBEM_HD inline void cut_in_mixed(const PointCol& P, const FaceF& Fc, const floa
   o.g64[0] = F64.g[0]; o.g64[1] = F64.g[1];
   o.c = c;
   o.c64 = (double)c;
+  // the conic's size D0 = c^2 - d^2 (1 - |g|^2): where the cone only just
+  // reaches the face plane (|D0| < c^2 / 20) its two terms cancel, and c (an
+  // O(1) difference formed in FP32 pairs, but with <g, xb> in FP32) loses the
+  // relative accuracy D0 needs; there it is formed in FP64 from the apex's
+  // FP64 geometry (about 3 % of the cut faces)
+  const float d = P.F.d;
+  float D0 = c * c - d * d * (1.f - (Fc.g[0] * Fc.g[0] + Fc.g[1] * Fc.g[1]));
+  if (fabsf(D0) < 0.05f * c * c) {
+    const double c64 = P.t - (F64.p[0] + (F64.g[0] * P.D.xb[0] + F64.g[1] * P.D.xb[1]));
+    const double d64 = P.D.d;
+    D0 = (float)(c64 * c64 - d64 * d64 * (1.0 - (F64.g[0] * F64.g[0] + F64.g[1] * F64.g[1])));
+  }
+  o.D0 = D0;
 }
 
 // A conic arc of a cut face (d != 0) recorded for evaluation later: the
@@ -937,9 +958,9 @@ STBEM_HD inline void cut_in_mixed(const PointCol& P, const FaceF& Fc, const floa
 // of the far-field form (foot point xb, C, far_rho).
 template <typename R>
 struct ArcRec {
-  R A[2], dAB[2], c, d, g[2];
+  R A[2], dAB[2], c, d, g[2], D0;
   R xb[2], C, far_rho;
-  int full, tiny_is_short, far, pad;
+  int full, tiny_is_short, far;
 };
 
 // A far-field arc over its chord (arc_far), or conic_arc shifted from the
@@ -947,12 +968,12 @@ struct ArcRec {
 // (strongly curved arcs, or the long way round). A: start in column
 // coordinates.
 template <typename R>
-STBEM_HD inline R far_arc_value(const R* xb, R d, R C, R far_rho, R c, const R* g, const R* A, const R* dAB,
+STBEM_HD inline R far_arc_value(const R* xb, R d, R C, R far_rho, R c, const R* g, R D0, const R* A, const R* dAB,
                                 bool tiny_short, const ArcRule& rule, double c64, const double* g64) {
   R v;
   if (arc_far<R>(xb, d, C, far_rho, g, A, dAB, rule, v)) return v;
   const R ya[2] = {A[0] - xb[0], A[1] - xb[1]};
-  v = conic_arc<R>(ya, dAB, false, c, d, g, rule, c64, g64, tiny_short);
+  v = conic_arc<R>(ya, dAB, false, c, d, g, D0, rule, c64, g64, tiny_short);
   const R bx = ya[0] + dAB[0], by = ya[1] + dAB[1];
   const R dphi = atan2(ya[0] * by - ya[1] * bx, ya[0] * bx + ya[1] * by);
   return v - (xb[0] * xb[0] + xb[1] * xb[1]) / (C + fabs(d)) * dphi;
@@ -961,9 +982,9 @@ STBEM_HD inline R far_arc_value(const R* xb, R d, R C, R far_rho, R c, const R* 
 template <typename R>
 STBEM_HD inline R arc_value(const ArcRec<R>& a, const ArcRule& rule) {
   if (a.far)
-    return far_arc_value<R>(a.xb, a.d, a.C, a.far_rho, a.c, a.g, a.A, a.dAB, a.tiny_is_short != 0, rule, 0.0,
+    return far_arc_value<R>(a.xb, a.d, a.C, a.far_rho, a.c, a.g, a.D0, a.A, a.dAB, a.tiny_is_short != 0, rule, 0.0,
                             nullptr);
-  return conic_arc<R>(a.full ? nullptr : a.A, a.full ? nullptr : a.dAB, a.full != 0, a.c, a.d, a.g, rule, 0.0,
+  return conic_arc<R>(a.full ? nullptr : a.A, a.full ? nullptr : a.dAB, a.full != 0, a.c, a.d, a.g, a.D0, rule, 0.0,
                       nullptr, a.tiny_is_short != 0);
 }
 
@@ -1053,7 +1074,7 @@ STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, con
         if (ev_in[j]) {
           R dAB[2] = {ev_l[j][0] - ev_l[i][0], ev_l[j][1] - ev_l[i][1]};
           if (P.far && !(defer && d != R(0))) {
-            total += far_arc_value<R>(P.xb, d, P.C, P.far_rho, c, g, ev_l[i], dAB, tiny_short, rule, in.c64,
+            total += far_arc_value<R>(P.xb, d, P.C, P.far_rho, c, g, in.D0, ev_l[i], dAB, tiny_short, rule, in.c64,
                                       in.g64);
             break;
           }
@@ -1067,9 +1088,9 @@ STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, con
               a.A[0] = ev_y[i][0]; a.A[1] = ev_y[i][1];
             }
             a.dAB[0] = dAB[0]; a.dAB[1] = dAB[1];
-            a.c = c; a.d = d; a.g[0] = g[0]; a.g[1] = g[1]; a.full = 0; a.tiny_is_short = tiny_short;
+            a.c = c; a.d = d; a.g[0] = g[0]; a.g[1] = g[1]; a.D0 = in.D0; a.full = 0; a.tiny_is_short = tiny_short;
           } else {
-            total += conic_arc<R>(ev_y[i], dAB, false, c, d, g, rule, in.c64, in.g64, tiny_short);
+            total += conic_arc<R>(ev_y[i], dAB, false, c, d, g, in.D0, rule, in.c64, in.g64, tiny_short);
           }
           break;
         }
@@ -1078,7 +1099,7 @@ STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, con
   } else {
     // no crossing: E inside K (closed ellipse) or E cap K empty
     R G2 = g[0] * g[0] + g[1] * g[1];
-    if (!(G2 < R(1) && c > fabs(d) * sqrt(R(1) - G2))) return 0.0;
+    if (!(G2 < R(1) && c > R(0) && in.D0 > R(0))) return 0.0;   // c > |d| sqrt(1 - |g|^2)
     R G0 = sqrt(G2);
     R sst = G0 > R(0) ? fabs(d) * G0 / sqrt(R(1) - G2) : R(0);
     R yst[2] = {G0 > R(0) ? -sst * g[0] / G0 : R(0), G0 > R(0) ? -sst * g[1] / G0 : R(0)};
@@ -1089,9 +1110,9 @@ STBEM_HD __noinline__ double face_cut(const ColR<R>& G, const PointCol& P64, con
     if (defer && d != R(0)) {
       ArcRec<R>& a = defer[(*ndefer)++];
       a.A[0] = a.A[1] = a.dAB[0] = a.dAB[1] = R(0);
-      a.c = c; a.d = d; a.g[0] = g[0]; a.g[1] = g[1]; a.full = 1; a.tiny_is_short = 0; a.far = 0;
+      a.c = c; a.d = d; a.g[0] = g[0]; a.g[1] = g[1]; a.D0 = in.D0; a.full = 1; a.tiny_is_short = 0; a.far = 0;
     } else {
-      total += conic_arc<R>(nullptr, nullptr, true, c, d, g, rule, in.c64, in.g64);
+      total += conic_arc<R>(nullptr, nullptr, true, c, d, g, in.D0, rule, in.c64, in.g64);
     }
   }
   return (double)total;
