@@ -423,6 +423,7 @@ bem_status stbem::op_structure_alloc(bem_context* ctx, const bem_mesh* mesh, con
   op->mq = o.m_q; op->nq = o.m_q * o.m_q; op->n_theta = o.n_theta;
   const int64_t nb = mesh->n_col * mesh->n_col;
   TRY(dalloc(&op->d_pts, (size_t)mesh->n_surf * op->nq * 4));
+  TRY(dalloc(&op->d_ptsf, (size_t)mesh->n_surf * op->nq * 4));
   TRY(dalloc(&op->d_pts_trange, (size_t)mesh->n_surf * 2));
   TRY(dalloc(&op->d_bw, (size_t)nb));
   TRY(dalloc(&op->d_bnnz, (size_t)nb));
@@ -575,7 +576,7 @@ bem_status bem_operator_stats(const bem_operator* op, int64_t* nnz, int64_t* sto
 
 void bem_operator_destroy(bem_operator* op) {
   if (!op) return;
-  cudaFree(op->d_pts); cudaFree(op->d_pts_trange); cudaFree(op->d_bw); cudaFree(op->d_bnnz);
+  cudaFree(op->d_pts); cudaFree(op->d_ptsf); cudaFree(op->d_pts_trange); cudaFree(op->d_bw); cudaFree(op->d_bnnz);
   cudaFree(op->d_boff); cudaFree(op->d_rsoff); cudaFree(op->d_rs); cudaFree(op->d_val);
   cudaFree(op->d_val32); cudaFree(op->d_tmp); cudaFree(op->d_counter);
   cudaFree(op->d_val16); cudaFree(op->d_ws); cudaFree(op->d_pv);

@@ -61,8 +61,13 @@ bem_status upload_gauss_tables() {
   }
   std::copy(X.begin(), X.end(), h_gl_x);
   std::copy(W.begin(), W.end(), h_gl_w);
+  std::vector<float> Xf(X.begin(), X.end()), Wf(W.begin(), W.end());
+  std::copy(Xf.begin(), Xf.end(), h_gl_xf);
+  std::copy(Wf.begin(), Wf.end(), h_gl_wf);
   STBEM_CUDA(cudaMemcpyToSymbol(c_gl_x, X.data(), X.size() * sizeof(double)));
   STBEM_CUDA(cudaMemcpyToSymbol(c_gl_w, W.data(), W.size() * sizeof(double)));
+  STBEM_CUDA(cudaMemcpyToSymbol(c_gl_xf, Xf.data(), Xf.size() * sizeof(float)));
+  STBEM_CUDA(cudaMemcpyToSymbol(c_gl_wf, Wf.data(), Wf.size() * sizeof(float)));
   return BEM_OK;
 }
 
@@ -128,7 +133,7 @@ bem_status mesh_device_geometry(bem_mesh* m, const double* d_sv_xyz, const int32
 // id) and x = (A + xi1 (B - A)) + xi2 (C - A) without fused operations.
 // ---------------------------------------------------------------------------
 __global__ void k_outer_points(int64_t n_surf, int mq, const ColGeom* cols, const SurfDev* surf, double* pts,
-                               double* trange) {
+                               float* ptsf, double* trange) {
   int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n_surf) return;
   const SurfDev S = surf[s];
@@ -149,6 +154,7 @@ __global__ void k_outer_points(int64_t n_surf, int mq, const ColGeom* cols, cons
         for (int d = 0; d < 4; ++d) {
           double p = __dadd_rn(A[d], __dmul_rn(x1, __dsub_rn(B[d], A[d])));
           out[4 * n + d] = __dadd_rn(p, __dmul_rn(x2, __dsub_rn(C[d], A[d])));
+          ptsf[(int64_t)s * nq * 4 + 4 * n + d] = (float)out[4 * n + d];
         }
         tlo = fmin(tlo, out[4 * n]);
         thi = fmax(thi, out[4 * n]);
@@ -163,7 +169,7 @@ bem_status op_outer_points(bem_operator* op, cudaStream_t s) {
   const bem_mesh* m = op->mesh;
   int th = 128;
   k_outer_points<<<(unsigned)((m->n_surf + th - 1) / th), th, 0, s>>>(m->n_surf, op->mq, m->d_col, m->d_surf,
-                                                                      op->d_pts, op->d_pts_trange);
+                                                                      op->d_pts, op->d_ptsf, op->d_pts_trange);
   STBEM_CUDA(cudaGetLastError());
   return BEM_OK;
 }
@@ -292,6 +298,7 @@ struct BlockCtx {
   const SurfDev* surf;
   const TetDev* tets;
   const double* pts;
+  const float* ptsf;
   const double* trange;
   int32_t* bw;
   int64_t* bnnz;
@@ -353,14 +360,15 @@ __device__ void face_bits(const BlockCtx& B, const ColSm& C, const TetSm* T, int
   for (int w = lane; w < words; w += 32) bits[w] = 0u;
   __syncwarp();
   const double* P = B.pts + fglob * B.nq * 4;
+  const float* Pf = B.ptsf + fglob * B.nq * 4;   // FP32 copies: no conversions in the filter
   for (int j0 = jlo; j0 < jhi; j0 += 32) {
     int j = j0 + lane;
     bool hit = false;
     if (j < jhi) {
       for (int q = 0; q < B.nq && !hit; ++q) {
-        const double* x = P + 4 * q;
-        float xf[4] = {(float)x[0], (float)x[1], (float)x[2], (float)x[3]};
-        hit = point_sees(x, xf, T[j], C.G, C.Xf, B.margin);
+        const float4 x4 = reinterpret_cast<const float4*>(Pf)[q];
+        const float xf[4] = {x4.x, x4.y, x4.z, x4.w};
+        hit = point_sees(P + 4 * q, xf, T[j], C.G, C.Xf, B.margin);
       }
     }
     unsigned m = __ballot_sync(0xffffffffu, hit);
@@ -560,7 +568,11 @@ __device__ __forceinline__ void quad_block(const BlockCtx& B, int64_t b, unsigne
       const int nsw = shi - slo + 1;
       // per-point geometry against column J
       const double* P = B.pts + fg * B.nq * 4;
-      for (int q = lane; q < B.nq; q += 32) point_col(P + 4 * q, C.G, mypc[q], FP32, FP32);
+      if constexpr (FP32) {
+        for (int q = lane; q < B.nq; q += 32) point_col(P + 4 * q, C.G, mypc[q], true, true, &CR);
+      } else {
+        for (int q = lane; q < B.nq; q += 32) point_col(P + 4 * q, C.G, mypc[q], false);
+      }
       if constexpr (FP32) {
         // the whole-edge integrals of the points' fully lit triangle, lane per (point, edge)
         __syncwarp();
@@ -811,7 +823,7 @@ static BlockCtx make_ctx(bem_operator* op) {
   B.S = m->coord_scale;
   B.margin = (float)(1.6e-5 * m->coord_scale);  // > 4x the FP32 error bound of C2 and C3
   B.cols = m->d_col; B.col_tet_begin = m->d_col_tet_begin; B.col_surf_begin = m->d_col_surf_begin;
-  B.surf = m->d_surf; B.tets = m->d_tet; B.pts = op->d_pts; B.trange = op->d_pts_trange;
+  B.surf = m->d_surf; B.tets = m->d_tet; B.pts = op->d_pts; B.ptsf = op->d_ptsf; B.trange = op->d_pts_trange;
   B.bw = op->d_bw; B.bnnz = op->d_bnnz; B.boff = op->d_boff; B.rsoff = op->d_rsoff; B.rs = op->d_rs;
   B.val = op->d_val; B.val32 = op->d_val32; B.uscratch = op->d_tmp;
   B.max_surf = m->max_col_surf; B.max_tet = m->max_col_tets;

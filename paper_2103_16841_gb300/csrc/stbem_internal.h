@@ -77,6 +77,7 @@ struct bem_operator {
   bem_op_opts opts{};
   int mq = 3, nq = 9, n_theta = 12;
   double* d_pts = nullptr;       // [n_surf][nq][4] outer points
+  float* d_ptsf = nullptr;       // the same rounded to FP32 (the sparsity filter's inputs)
   double* d_pts_trange = nullptr;// [n_surf][2] min / max time of the outer points
   int32_t* d_bw = nullptr;       // [n_col*n_col] band width per column block
   int64_t* d_bnnz = nullptr;     // [n_col*n_col] pattern entries per block

@@ -66,6 +66,38 @@ STBEM_HD inline const double* gl_w() {
 #endif
 }
 
+// the same tables rounded to FP32 for the FP32 rules (no conversion per node)
+static __constant__ float c_gl_xf[MAX_NTHETA * (MAX_NTHETA + 1) / 2];
+static __constant__ float c_gl_wf[MAX_NTHETA * (MAX_NTHETA + 1) / 2];
+static float h_gl_xf[MAX_NTHETA * (MAX_NTHETA + 1) / 2];
+static float h_gl_wf[MAX_NTHETA * (MAX_NTHETA + 1) / 2];
+
+// nodes / weights of rule n in precision R
+template <typename R>
+STBEM_HD inline const R* gl_nodes(int n);
+template <typename R>
+STBEM_HD inline const R* gl_weights(int n);
+template <>
+STBEM_HD inline const double* gl_nodes<double>(int n) { return gl_x() + n * (n - 1) / 2; }
+template <>
+STBEM_HD inline const double* gl_weights<double>(int n) { return gl_w() + n * (n - 1) / 2; }
+template <>
+STBEM_HD inline const float* gl_nodes<float>(int n) {
+#ifdef __CUDA_ARCH__
+  return c_gl_xf + n * (n - 1) / 2;
+#else
+  return h_gl_xf + n * (n - 1) / 2;
+#endif
+}
+template <>
+STBEM_HD inline const float* gl_weights<float>(int n) {
+#ifdef __CUDA_ARCH__
+  return c_gl_wf + n * (n - 1) / 2;
+#else
+  return h_gl_wf + n * (n - 1) / 2;
+#endif
+}
+
 struct ColGeom {         // per spatial triangle ("column"), column frame
   double X[3][3];        // corners (input coordinates), ascending spatial-vertex id
   double c0[3];          // corner 0
@@ -160,14 +192,37 @@ STBEM_HD inline const PtR<float>& pt<float>(const PointCol& P) { return P.F; }
 struct ArcRule {
   int nmin, nmax;    // Gauss node bounds per piece
   double tol;        // target relative accuracy of a piece
+  float ltol_f;      // log(1 / tol), kept so that no rule choice divides or
+  double ltol_d;     // takes a logarithm in FP64 at run time
+  int fp32_short;    // FP32 shortcut of arc_piece allowed (nmin >= 4, tol >= 1 / 1.6e7)
 };
 
+STBEM_HD inline void rule_finish(ArcRule& r) {
+  r.ltol_d = log(1.0 / r.tol);
+  r.ltol_f = (float)r.ltol_d;
+  r.fp32_short = r.nmin >= 4 && r.tol >= 1.0 / 1.6e7;
+}
+
+// log(1 / tol) of a rule in precision R
+template <typename R>
+STBEM_HD inline R rule_ltol(const ArcRule& r);
+template <>
+STBEM_HD inline float rule_ltol<float>(const ArcRule& r) { return r.ltol_f; }
+template <>
+STBEM_HD inline double rule_ltol<double>(const ArcRule& r) { return r.ltol_d; }
+
 // n_max = 0 selects the default cap (32 nodes FP64, 16 nodes MIXED).
+// (log(1e7) and log(1e15) written out: this is called per point and column)
 STBEM_HD inline ArcRule make_rule(int precision_mixed, int n_max) {
   ArcRule r;
-  if (precision_mixed) { r.nmin = 4; r.nmax = n_max ? n_max : 16; r.tol = 1e-7; }
-  else { r.nmin = 6; r.nmax = n_max ? n_max : 32; r.tol = 1e-15; }
+  if (precision_mixed) {
+    r.nmin = 4; r.nmax = n_max ? n_max : 16; r.tol = 1e-7; r.ltol_d = 16.11809565095832;
+  } else {
+    r.nmin = 6; r.nmax = n_max ? n_max : 32; r.tol = 1e-15; r.ltol_d = 34.538776394910684;
+  }
   if (r.nmin > r.nmax) r.nmin = r.nmax;
+  r.ltol_f = (float)r.ltol_d;
+  r.fp32_short = r.nmin >= 4 && precision_mixed;
   return r;
 }
 
@@ -226,11 +281,11 @@ STBEM_HD inline bool edge_gauss(R wa, R dw, R p_s, R d, const ArcRule& rule, R& 
   R s = R(0.5) * (sqrt((a - R(1)) * (a - R(1)) + b * b) + sqrt((a + R(1)) * (a + R(1)) + b * b));
   R rho = s + sqrt(fmax(s * s - R(1), R(0)));
   if (!(rho >= R(4))) return false;
-  int n = (int)ceil(log(R(1.0 / rule.tol)) / (R(2) * log(rho))) + 1;
+  int n = (int)ceil(rule_ltol<R>(rule) / (R(2) * log(rho))) + 1;
   if (n > 6) return false;   // the closed form costs about as much as six nodes
   n = n < 2 ? 2 : n;
-  const double* X = gl_x() + n * (n - 1) / 2;
-  const double* Wt = gl_w() + n * (n - 1) / 2;
+  const R* X = gl_nodes<R>(n);
+  const R* Wt = gl_weights<R>(n);
   R ad = fabs(d), acc = R(0);
   for (int k = 0; k < n; ++k) {
     R w = m + hl * (R)X[k];
@@ -272,11 +327,11 @@ constexpr float FAR_RHO = 1.5f;
 // Gauss-Legendre order reaching relative accuracy tol on [-1, 1] for an
 // integrand analytic except at z = a +- i b (Bernstein ellipse parameter)
 template <typename R>
-STBEM_HD inline int gauss_order(R a, R b, double tol, int nmin, int nmax) {
+STBEM_HD inline int gauss_order(R a, R b, R ltol, int nmin, int nmax) {
   const R s = R(0.5) * (sqrt((a - R(1)) * (a - R(1)) + b * b) + sqrt((a + R(1)) * (a + R(1)) + b * b));
   const R rho = s + sqrt(fmax(s * s - R(1), R(0)));
   if (!(rho > R(1.0001))) return nmax;
-  const int n = (int)ceil(log((R)(1.0 / tol)) / (R(2) * log(rho))) + 1;
+  const int n = (int)ceil(ltol / (R(2) * log(rho))) + 1;
   return n < nmin ? nmin : (n > nmax ? nmax : n);
 }
 
@@ -290,9 +345,9 @@ STBEM_HD inline R edge_far(const PtR<R>& P, const ColR<R>& G, int k, R la, R lb,
   const R mid = R(0.5) * (la + lb), L = G.L[k];
   const R q0x = -P.xb[0], q0y = -P.xb[1];
   // |q|^2 = 0 at lambda = lambda_foot +- i |p_s| / L
-  const int n = gauss_order<R>((-P.ws[k] / L - mid) / h, fabs(P.ps[k]) / (L * h), rule.tol, 3, 10);
-  const double* X = gl_x() + n * (n - 1) / 2;
-  const double* Wt = gl_w() + n * (n - 1) / 2;
+  const int n = gauss_order<R>((-P.ws[k] / L - mid) / h, fabs(P.ps[k]) / (L * h), rule_ltol<R>(rule), 3, 10);
+  const R* X = gl_nodes<R>(n);
+  const R* Wt = gl_weights<R>(n);
   const R ex = G.U[k][0] * L, ey = G.U[k][1] * L, d2 = P.d * P.d;
   R acc = R(0);
   for (int i = 0; i < n; ++i) {
@@ -343,9 +398,9 @@ STBEM_HD inline bool arc_far(const R* xb, R d, R C, R far_rho, const R* g, const
   }
   const R delA = (uA[0] * (R(2) * q0x + uA[0]) + uA[1] * (R(2) * q0y + uA[1])) / (rA + C);
   // |q|^2 has no zero within far_rho of the chord (it lies in K)
-  const int n = gauss_order<R>(R(0), R(2) * far_rho / l, rule.tol, 4, 10);
-  const double* X = gl_x() + n * (n - 1) / 2;
-  const double* Wt = gl_w() + n * (n - 1) / 2;
+  const int n = gauss_order<R>(R(0), R(2) * far_rho / l, rule_ltol<R>(rule), 4, 10);
+  const R* X = gl_nodes<R>(n);
+  const R* Wt = gl_weights<R>(n);
   R acc = R(0);
   for (int i = 0; i < n; ++i) {
     const R sv = R(0.5) * (R(1) + (R)X[i]);
@@ -390,7 +445,7 @@ STBEM_HD inline float edge_full_mixed(const PointCol& P, const ColR<float>& CR, 
 // the caller (edge_full_mixed per edge, then point_col_finish), so that a warp
 // can spread the three edges of its points over its lanes.
 STBEM_HD inline void point_col(const double* x, const ColGeom& G, PointCol& P, bool prec_fp32,
-                               bool defer_edges = false) {
+                               bool defer_edges = false, const ColR<float>* CRf = nullptr) {
   P.t = x[0];
   double rel[3] = {x[1] - G.c0[0], x[2] - G.c0[1], x[3] - G.c0[2]};
   double d = rel[0] * G.n[0] + rel[1] * G.n[1] + rel[2] * G.n[2];
@@ -408,20 +463,21 @@ STBEM_HD inline void point_col(const double* x, const ColGeom& G, PointCol& P, b
     T.xb[1] = (float)xb1;
     int in = 1;
     float out = 0.f, W = 0.f;
+    // (the column's FP32 frame from CRf when given: no conversions per point)
     for (int k = 0; k < 3; ++k) {
-      T.q[k][0] = (float)G.Q[k][0] - T.xb[0];
-      T.q[k][1] = (float)G.Q[k][1] - T.xb[1];
+      T.q[k][0] = (CRf ? CRf->Q[k][0] : (float)G.Q[k][0]) - T.xb[0];
+      T.q[k][1] = (CRf ? CRf->Q[k][1] : (float)G.Q[k][1]) - T.xb[1];
       T.rs[k] = (float)P.r[k];
     }
     for (int k = 0; k < 3; ++k) {
-      float ux = (float)G.U[k][0], uy = (float)G.U[k][1];
+      float ux = CRf ? CRf->U[k][0] : (float)G.U[k][0], uy = CRf ? CRf->U[k][1] : (float)G.U[k][1];
       T.ps[k] = T.q[k][0] * uy - T.q[k][1] * ux;
       T.ws[k] = T.q[k][0] * ux + T.q[k][1] * uy;
       if (!(T.ps[k] > 0.f)) in = 0;
       out = fmaxf(out, -T.ps[k]);
       split2(P.r[k] - P.t, P.rho_hi[k], P.rho_lo[k]);
     }
-    T.far = out >= FAR_RHO * (float)G.diam;
+    T.far = out >= FAR_RHO * (CRf ? CRf->diam : (float)G.diam);
     T.C = T.rs[0];
     T.far_rho = out;
     if (!defer_edges) {
@@ -641,7 +697,7 @@ STBEM_HD __noinline__ R arc_piece(const ArcFrame<R>& F, R lo, R hi, const ArcRul
       const R fm = fmin(fabs(f1), fabs(f2));
       far_poles = !(A1 > R(0)) || R(2) * asinh(fm / A1) >= R(16) * half;
       // Gauss error ~ R^(-2n): R >= 15.9 and n_min >= 4 reach 15.9^-6 < 1/1.6e7
-      far_poles = far_poles && rule.nmin >= 4 && rule.tol >= 1.0 / 1.6e7;
+      far_poles = far_poles && rule.fp32_short;
     }
     if (!far_poles) {
       consider_pole<R>(R(1) - F.ca * gw, F.sa * ga, F.sa * gb, mid, half, best_rho, best_a, best_b);
@@ -661,8 +717,8 @@ STBEM_HD __noinline__ R arc_piece(const ArcFrame<R>& F, R lo, R hi, const ArcRul
   R acc = R(0);
   if (best_b < R(0.3)) {
     const int n = rule.nmax;
-    const double* X = gl_x() + n * (n - 1) / 2;
-    const double* Wt = gl_w() + n * (n - 1) / 2;
+    const R* X = gl_nodes<R>(n);
+    const R* Wt = gl_weights<R>(n);
     R a = best_a, b = best_b;
     if (a > R(1)) { b = sqrt((a - R(1)) * (a - R(1)) + b * b); a = R(1); }
     else if (a < R(-1)) { b = sqrt((a + R(1)) * (a + R(1)) + b * b); a = R(-1); }
@@ -679,11 +735,11 @@ STBEM_HD __noinline__ R arc_piece(const ArcFrame<R>& F, R lo, R hi, const ArcRul
   } else {
     int n = rule.nmin;
     if (best_rho < R(1e29)) {
-      int need = (int)ceil(log(R(1.0 / rule.tol)) / (R(2) * log(best_rho))) + 1;
+      int need = (int)ceil(rule_ltol<R>(rule) / (R(2) * log(best_rho))) + 1;
       n = need < rule.nmin ? rule.nmin : (need > rule.nmax ? rule.nmax : need);
     }
-    const double* X = gl_x() + n * (n - 1) / 2;
-    const double* Wt = gl_w() + n * (n - 1) / 2;
+    const R* X = gl_nodes<R>(n);
+    const R* Wt = gl_weights<R>(n);
     for (int k = 0; k < n; ++k) acc += (R)Wt[k] * E(half * (R)X[k]);
   }
   return acc * half;
@@ -1147,11 +1203,19 @@ STBEM_HD inline double face_W(const ColGeom& G, const PointCol& P, const FaceGeo
 }
 
 // 4 pi W_P(x) entirely in FP64 from the apex coordinates: the fallback of the
-// mixed path for faces whose FP32 evaluation is not finite (see conic_arc)
+// mixed path for near-singular faces and for faces whose FP32 evaluation is
+// not finite (see conic_arc). The arc rule aims at 1e-10 (the mixed operator's
+// target is 1e-7): pieces away from a pole take fewer nodes than the FP64
+// operator's 1e-15 rule needs.
 STBEM_HD __noinline__ inline double face_W_fp64(const double* x, const ColGeom& G, const FaceGeom& Fc, int n_theta) {
   PointCol P;
   point_col(x, G, P, false);
-  return face_W<false>(G, P, Fc, make_rule(0, n_theta));
+  ArcRule r;
+  r.nmin = 4;
+  r.nmax = n_theta ? n_theta : 32;   // pieces next to a pole (sinh map) take nmax
+  r.tol = 1e-10;
+  rule_finish(r);
+  return face_W<false>(G, P, Fc, r);
 }
 
 }  // namespace stbem

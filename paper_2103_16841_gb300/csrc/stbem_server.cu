@@ -178,7 +178,7 @@ bem_status acquire(bem_server* S, uint64_t ticket, int64_t bytes) {
 int64_t structure_bytes(const bem_mesh* m) {
   const int64_t nb = m->n_col * m->n_col;
   return m->n_tet * (int64_t)(sizeof(TetDev) + 4 + 16 * 8) + m->n_col * (int64_t)(sizeof(ColGeom) + 8) +
-         m->n_surf * (int64_t)(sizeof(SurfDev) + (MAX_NQ * 4 + 2) * 8) + nb * (4 + 8 + 8 + 8);
+         m->n_surf * (int64_t)(sizeof(SurfDev) + (MAX_NQ * 4 + 2) * 8 + MAX_NQ * 4 * 4) + nb * (4 + 8 + 8 + 8);
 }
 
 // operator values + solver workspace for nrhs right-hand sides
