@@ -99,6 +99,25 @@ const char* bem_version(void);
  * all); synchronizes the context stream. */
 bem_status bem_alu_peaks(bem_context* ctx, double* fp32_tflops, double* fp64_tflops);
 
+/* Launch-shape autotuning of the persistent quadrature (no counterpart in the
+ * paper): the number of CTAs per SM it runs with. mode 0 (default): the
+ * occupancy limit of the build. mode 1: the first assembly of every shape
+ * class (device, precision, m_Q^2, rule order, largest column sizes, number
+ * of columns to within a factor 2) on this context times each candidate on
+ * 1/32 of the block queue and keeps the fastest; choices are kept for the
+ * process and, when cache_path is not NULL, read from and appended to that
+ * text file. Values do not depend on the shape (bit-identical either way).
+ * Matrix-free operators keep the default. Operators take the context's mode
+ * when they are assembled. */
+bem_status bem_context_set_tuning(bem_context* ctx, int mode, const char* cache_path);
+
+/* Self-test of the bounded device waits (no counterpart in the paper): one
+ * thread waits, with the clock budget of the tensor-core product's mbarrier
+ * waits cut to about 2e6 cycles, on a barrier that nothing completes. Returns
+ * BEM_ERR_DEVICE_TIMEOUT with waited_ms (may be NULL) = the time waited, and
+ * the context stays usable; any other status is a failure of the mechanism. */
+bem_status bem_selftest_bounded_wait(bem_context* ctx, double* waited_ms);
+
 /* ------------------------------------------------------------------ */
 /* Space-time mesh of Sigma (Sec. 3: Sigma_N of open tetrahedra)        */
 /* ------------------------------------------------------------------ */
@@ -177,8 +196,17 @@ bem_status bem_operator_stats(const bem_operator* op, int64_t* nnz_pattern, int6
  * (a face shared by two test panels counted once). Counted by the pattern pass. */
 bem_status bem_operator_work(const bem_operator* op, int64_t* inner_integrals);
 
+/* The quadrature's launch shape: CTAs per SM, how it was chosen (0 default,
+ * 1 timed in this assembly, 2 taken from the tuning cache) and, when timed,
+ * the sample time in ms of each candidate (index = CTAs per SM - 1; 0 where
+ * not timed). Any pointer may be NULL; sample_ms has 8 entries. */
+bem_status bem_operator_tuning(const bem_operator* op, int* ctas_per_sm, int* tuned, double* sample_ms);
+
 /* Scans the stored values on the device: number of non-finite values (NaN,
- * Inf) and the largest magnitude. A healthy operator has n_nonfinite = 0. */
+ * Inf) and the largest magnitude. A healthy operator has n_nonfinite = 0.
+ * Returns BEM_ERR_DEVICE_TIMEOUT (outputs still set) when a TF32 / BF16
+ * product of the operator gave up waiting for its own pipeline (every wait
+ * in that kernel is bounded); that product's output was set to NaN. */
 bem_status bem_operator_check(const bem_operator* op, int64_t* n_nonfinite, double* max_abs);
 
 /* Device time of the last assembly by phase (CUDA events on the assembly

@@ -11,6 +11,7 @@ the library has not been built.
 from __future__ import annotations
 
 import ctypes
+import os
 
 import numpy as np
 
@@ -45,6 +46,19 @@ class Context:
         a, b = ctypes.c_double(), ctypes.c_double()
         _lib.check(self._L.bem_alu_peaks(self.h, ctypes.byref(a), ctypes.byref(b)))
         return {"fp32_tflops": a.value, "fp64_tflops": b.value}
+
+    def selftest_bounded_wait(self):
+        """bem_selftest_bounded_wait: (status, ms waited); status 5
+        (BEM_ERR_DEVICE_TIMEOUT) is the expected outcome."""
+        ms = ctypes.c_double()
+        st = self._L.bem_selftest_bounded_wait(self.h, ctypes.byref(ms))
+        return int(st), ms.value
+
+    def set_tuning(self, mode=1, cache_path=None):
+        """bem_context_set_tuning: 1 = time the quadrature's launch shape per
+        shape class on first assembly (kept in cache_path if given), 0 = off."""
+        path = None if cache_path is None else os.fsencode(cache_path)
+        _lib.check(self._L.bem_context_set_tuning(self.h, int(mode), path))
 
     @staticmethod
     def version():
@@ -125,6 +139,14 @@ class Operator:
         n = np.zeros(1, dtype=np.int64)
         _lib.check(self.ctx._L.bem_operator_work(self.h, _lib.lptr(n)))
         return int(n[0])
+
+    def tuning(self):
+        """The quadrature's launch shape (bem_operator_tuning)."""
+        per, how = ctypes.c_int(), ctypes.c_int()
+        ms = np.zeros(8)
+        _lib.check(self.ctx._L.bem_operator_tuning(self.h, ctypes.byref(per), ctypes.byref(how), _lib.dptr(ms)))
+        return {"ctas_per_sm": per.value, "tuned": ["default", "timed", "cache"][how.value],
+                "sample_ms": {k + 1: float(v) for k, v in enumerate(ms) if v > 0}}
 
     def check(self):
         """(number of non-finite stored values, largest |value|)"""

@@ -26,6 +26,7 @@ DATA_PULSE = 1
 # every symbol include/stbem.h declares
 EXPORTS = [
     "bem_context_create", "bem_context_destroy", "bem_last_error", "bem_version", "bem_alu_peaks",
+    "bem_context_set_tuning", "bem_operator_tuning", "bem_selftest_bounded_wait",
     "bem_mesh_create", "bem_mesh_create_prisms", "bem_mesh_info", "bem_mesh_destroy",
     "bem_operator_create", "bem_operator_stats", "bem_operator_check", "bem_operator_work", "bem_operator_timings", "bem_operator_reassemble", "bem_operator_export_pattern", "bem_operator_pattern_rows",
     "bem_operator_export_dense", "bem_operator_entries", "bem_operator_destroy",
@@ -116,6 +117,9 @@ def load(build_if_missing: bool = False):
     L.bem_context_create.argtypes = [ctypes.c_int, ctypes.POINTER(VP)]
     L.bem_context_destroy.argtypes = [VP]
     L.bem_alu_peaks.argtypes = [VP, D, D]
+    L.bem_context_set_tuning.argtypes = [VP, ctypes.c_int, ctypes.c_char_p]
+    L.bem_selftest_bounded_wait.argtypes = [VP, D]
+    L.bem_operator_tuning.argtypes = [VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), D]
     L.bem_context_destroy.restype = None
     L.bem_mesh_create.argtypes = [VP, ctypes.c_int64, D, ctypes.c_int64, I32, D, ctypes.c_int64, I32,
                                   ctypes.POINTER(VP)]

@@ -21,7 +21,6 @@
 namespace stbem {
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
-int quad_grid(const bem_operator* op);
 }  // namespace stbem
 
 using namespace stbem;
@@ -375,7 +374,7 @@ bem_status stbem::op_layout(bem_operator* op, const int32_t* bw, const int64_t* 
     op->nstored = vo; op->nrows_stored = ro; op->nnz = nnz; op->nblocks = nblk;
     op->max_bw = wmax;
     if (own_scratch) {
-      int grid = quad_grid(op);
+      const int64_t grid = (int64_t)op->ctx->sm_count * quad_max_per_sm(op);
       op->tmp_len = std::max<int64_t>((int64_t)grid * m->max_col_surf * m->max_col_tets, 2 * m->n_tet * 8);
     } else {
       op->tmp_len = 0;
@@ -385,8 +384,9 @@ bem_status stbem::op_layout(bem_operator* op, const int32_t* bw, const int64_t* 
     if (!op->opts.matrix_free) {
       // mixed-precision values carry FP32 accuracy: FP32 storage only
       if (op->opts.precision == BEM_PREC_FP64) TRY(dalloc(&op->d_val, (size_t)vo));
-      if (op->opts.store_fp32 || op->opts.precision == BEM_PREC_MIXED) TRY(dalloc(&op->d_val32, (size_t)vo));
-      TRY(dalloc(&op->d_rs, (size_t)ro));
+      // (8 floats of tail room: the tensor-core product copies whole 16-byte granules)
+      if (op->opts.store_fp32 || op->opts.precision == BEM_PREC_MIXED) TRY(dalloc(&op->d_val32, (size_t)vo + 8));
+      TRY(dalloc(&op->d_rs, (size_t)ro + 4));   // (tail room as for the values)
     }
     if (own_scratch) TRY(dalloc(&op->d_tmp, (size_t)op->tmp_len));
   } else if ((!op->opts.matrix_free && vo != op->nstored) || nnz != op->nnz) {
@@ -460,6 +460,7 @@ bem_status assemble(bem_operator* op, cudaStream_t s, bool first) {
   TRY(op_layout(op, bw.data(), bnnz.data(), first, true, s));
   STBEM_CUDA(cudaEventRecord(ec, s));
   if (!op->opts.matrix_free) TRY(op_quadrature(op, s));
+  op->tcv_stale[0] = op->tcv_stale[1] = true;   // the tensor-core product's slots are remade on next use
   STBEM_CUDA(cudaEventRecord(e1, s));
   STBEM_CUDA(cudaEventSynchronize(e1));
   float ms = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
@@ -551,6 +552,12 @@ bem_status bem_operator_check(const bem_operator* op, int64_t* n_nonfinite, doub
   TRY(op_value_scan(op, &nb, &mx, op->ctx->stream));
   if (n_nonfinite) *n_nonfinite = nb;
   if (max_abs) *max_abs = mx;
+  int tc_flag = 0;
+  TRY(op_tc_error(op, &tc_flag));
+  if (tc_flag) {
+    set_error("a tensor-core product gave up waiting for its pipeline (its output was set to NaN)");
+    return BEM_ERR_DEVICE_TIMEOUT;
+  }
   return BEM_OK;
 }
 
@@ -579,7 +586,9 @@ void bem_operator_destroy(bem_operator* op) {
   cudaFree(op->d_pts); cudaFree(op->d_ptsf); cudaFree(op->d_pts_trange); cudaFree(op->d_bw); cudaFree(op->d_bnnz);
   cudaFree(op->d_boff); cudaFree(op->d_rsoff); cudaFree(op->d_rs); cudaFree(op->d_val);
   cudaFree(op->d_val32); cudaFree(op->d_tmp); cudaFree(op->d_counter);
-  cudaFree(op->d_val16); cudaFree(op->d_ws); cudaFree(op->d_pv);
+  cudaFree(op->d_ws); cudaFree(op->d_pv);
+  cudaFree(op->d_tc_colptr); cudaFree(op->d_tc_blk); cudaFree(op->d_tc_err);
+  cudaFree(op->d_tcv[0]); cudaFree(op->d_tcv[1]);
   delete op;
 }
 

@@ -310,6 +310,7 @@ struct BlockCtx {
   double* uscratch;     // [gridDim][max_surf][max_tet]
   int max_surf, max_tet;
   unsigned long long* counter;
+  int64_t end;                 // blocks [0, end) of the dense (I, J) order are processed
   unsigned long long* inner;   // pattern pass: inner integrals m_Q^2 x (test face, trial panel) (null: not counted)
   // matrix-free product: when mf_y is set the entries are not stored but
   // y[k][i] += A_ij x[k][j] is accumulated (x, y: [mf_nrhs][mf_ld], internal order)
@@ -738,7 +739,7 @@ __global__ void __launch_bounds__(128, STBEM_QUAD_MIN_CTAS) k_quad_blocks(BlockC
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ColSm C;
   __shared__ ColR<R> CR;
-  const int64_t nblk = B.n_col * B.n_col;
+  const int64_t nblk = B.end;
   for (;;) {
     int64_t b = pop_block(B.counter);
     if (b >= nblk) break;
@@ -828,6 +829,7 @@ static BlockCtx make_ctx(bem_operator* op) {
   B.val = op->d_val; B.val32 = op->d_val32; B.uscratch = op->d_tmp;
   B.max_surf = m->max_col_surf; B.max_tet = m->max_col_tets;
   B.counter = nullptr;
+  B.end = m->n_col * m->n_col;
   B.inner = nullptr;
   B.mf_x = nullptr; B.mf_y = nullptr; B.mf_nrhs = 0; B.mf_ld = m->n_tet;
   return B;
@@ -854,22 +856,27 @@ bem_status op_pattern(bem_operator* op, cudaStream_t s) {
   return BEM_OK;
 }
 
-int quad_grid(const bem_operator* op) {
-  size_t smem = block_smem(op, true);
-  if (op->opts.precision == BEM_PREC_MIXED) {
-    ensure_smem_attr((const void*)k_quad_blocks<true>, smem);
-    return persistent_grid((const void*)k_quad_blocks<true>, smem, 128);
-  }
-  ensure_smem_attr((const void*)k_quad_blocks<false>, smem);
-  return persistent_grid((const void*)k_quad_blocks<false>, smem, 128);
+int quad_max_per_sm(const bem_operator* op) {
+  const size_t smem = block_smem(op, true);
+  const void* kern = op->opts.precision == BEM_PREC_MIXED ? (const void*)k_quad_blocks<true>
+                                                          : (const void*)k_quad_blocks<false>;
+  ensure_smem_attr(kern, smem);
+  return std::max(1, persistent_grid(kern, smem, 128) / std::max(1, (int)op->ctx->sm_count));
 }
 
-bem_status op_quadrature(bem_operator* op, cudaStream_t s) {
-  BlockCtx B = make_ctx(op);
+bem_status quad_launch(const bem_operator* op, int per_sm, int64_t end, const double* mf_x, double* mf_y, int nrhs,
+                       cudaStream_t s) {
+  BlockCtx B = make_ctx(const_cast<bem_operator*>(op));
   bem_status st = get_counter(op, &B.counter, s);
   if (st != BEM_OK) return st;
-  size_t smem = block_smem(op, true);
-  int grid = quad_grid(op);
+  B.end = std::min<int64_t>(end, B.end);
+  B.mf_x = mf_x;
+  B.mf_y = mf_y;
+  B.mf_nrhs = nrhs;
+  B.mf_ld = op->mesh->n_tet;
+  const size_t smem = block_smem(op, true);
+  const int max_per = quad_max_per_sm(op);
+  const int grid = (int)op->ctx->sm_count * std::max(1, std::min(per_sm, max_per));
   if ((int64_t)grid * op->mesh->max_col_surf * op->mesh->max_col_tets > op->tmp_len) {
     set_error("quadrature scratch too small");
     return BEM_ERR_INTERNAL;
@@ -878,29 +885,20 @@ bem_status op_quadrature(bem_operator* op, cudaStream_t s) {
   else k_quad_blocks<false><<<grid, 128, smem, s>>>(B);
   STBEM_CUDA(cudaGetLastError());
   return BEM_OK;
+}
+
+bem_status op_quadrature(bem_operator* op, cudaStream_t s) {
+  bem_status st = choose_quad_shape(op, s);
+  if (st != BEM_OK) return st;
+  return quad_launch(op, op->quad_per_sm, op->mesh->n_col * op->mesh->n_col, nullptr, nullptr, 0, s);
 }
 
 // Matrix-free product y = A x (internal order, [nrhs][n_tet]): the quadrature
 // pass with the entries summed against x instead of stored.
 bem_status op_matvec_free(const bem_operator* op, const double* x, double* y, int nrhs, cudaStream_t s) {
-  BlockCtx B = make_ctx(const_cast<bem_operator*>(op));
-  bem_status st = get_counter(op, &B.counter, s);
-  if (st != BEM_OK) return st;
-  B.mf_x = x;
-  B.mf_y = y;
-  B.mf_nrhs = nrhs;
-  B.mf_ld = op->mesh->n_tet;
   STBEM_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * op->mesh->n_tet * nrhs, s));
-  size_t smem = block_smem(op, true);
-  int grid = quad_grid(op);
-  if ((int64_t)grid * op->mesh->max_col_surf * op->mesh->max_col_tets > op->tmp_len) {
-    set_error("quadrature scratch too small");
-    return BEM_ERR_INTERNAL;
-  }
-  if (op->opts.precision == BEM_PREC_MIXED) k_quad_blocks<true><<<grid, 128, smem, s>>>(B);
-  else k_quad_blocks<false><<<grid, 128, smem, s>>>(B);
-  STBEM_CUDA(cudaGetLastError());
-  return BEM_OK;
+  const int per_sm = op->quad_per_sm > 0 ? op->quad_per_sm : quad_max_per_sm(op);
+  return quad_launch(op, per_sm, op->mesh->n_col * op->mesh->n_col, x, y, nrhs, s);
 }
 
 // ---------------------------------------------------------------------------

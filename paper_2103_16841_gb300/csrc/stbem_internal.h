@@ -52,6 +52,8 @@ struct bem_context {
   int device = 0;
   cudaStream_t stream = nullptr;
   double sm_count = 0;
+  int tune_mode = 0;          // 1: launch shapes timed per shape class (bem_context_set_tuning)
+  std::string tune_path;      // text cache of the tuned shapes ("" = process only)
 };
 
 struct bem_mesh {
@@ -91,16 +93,27 @@ struct bem_operator {
   int max_bw = 0;                // widest band of any block
   double assemble_ms = 0.0;
   double phase_ms[4] = {0, 0, 0, 0};
+  int quad_per_sm = 0;           // CTAs per SM of the persistent quadrature (0: not chosen yet)
+  int quad_tuned = 0;            // 0 default shape, 1 timed here, 2 from the tuning cache
+  double tune_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // sample time per candidate (CTAs per SM = index + 1)
   unsigned long long* d_counter = nullptr;  // work counter of the persistent kernels
   // quadrature scratch
   double* d_tmp = nullptr;
   int64_t tmp_len = 0;
   // made on first use by the products (an operator is used by one host thread at a time)
-  mutable uint16_t* d_val16 = nullptr;  // BF16 copy of the values
   mutable float* d_ws = nullptr;        // packed operands of the FP32 / tensor-core products
   mutable int64_t ws_len = 0;
   mutable double* d_pv = nullptr;       // caller-order <-> internal-order vectors of the products
   mutable int64_t pv_len = 0;           // (stream-ordered allocation, grown on demand)
+  mutable int32_t* d_tc_colptr = nullptr;  // tensor-core product: non-empty blocks per test column
+  mutable void* d_tc_blk = nullptr;        // (TcBlk records, trial columns ascending)
+  mutable int64_t tc_nblk = 0;
+  mutable int tc_span[2] = {0, 0};         // widest band union of a block from a BF16 / TF32 chunk boundary
+  mutable void* d_tcv[2] = {nullptr, nullptr};  // values as chunk slots (BF16, TF32) of the tensor-core product
+  mutable int64_t tcv_len[2] = {0, 0};     // 16-byte slots of each
+  mutable int64_t tcv_cap[2] = {0, 0};     // bytes of the largest block's slots
+  mutable bool tcv_stale[2] = {false, false};   // the values were reassembled since the slots were made
+  mutable int* d_tc_err = nullptr;         // set when a tensor-core product gave up on a wait
   // optional admission hook, called once the sparsity structure is known
   // (nstored, nrows_stored, tmp_len set) and before the value arrays are allocated
   std::function<bem_status(const bem_operator*)> admit;
@@ -114,6 +127,14 @@ bem_status mesh_device_geometry(bem_mesh* m, const double* d_sv_xyz, const int32
 bem_status op_outer_points(bem_operator* op, cudaStream_t s);
 bem_status op_pattern(bem_operator* op, cudaStream_t s);
 bem_status op_quadrature(bem_operator* op, cudaStream_t s);
+// most CTAs of the quadrature kernel resident per SM (shared memory and registers)
+int quad_max_per_sm(const bem_operator* op);
+// one persistent quadrature launch with per_sm CTAs per SM over the blocks
+// [0, end) of the dense (I, J) order (assembled, or summed against mf_x)
+bem_status quad_launch(const bem_operator* op, int per_sm, int64_t end, const double* mf_x, double* mf_y, int nrhs,
+                       cudaStream_t s);
+// sets op->quad_per_sm: the context's tuning cache, a timed choice, or the default (stbem_tune.cu)
+bem_status choose_quad_shape(bem_operator* op, cudaStream_t s);
 // raise a kernel's dynamic shared-memory limit to at least `bytes` (never lowers it)
 bem_status ensure_smem_attr(const void* kern, size_t bytes);
 // matrix-free product (internal order): the quadrature pass summed against x
@@ -189,6 +210,15 @@ int64_t operator_value_bytes(const bem_operator* op);
 // arithmetic of a product (values equal to BEM_DTYPE_*)
 enum { MV_FP64 = 0, MV_FP32 = 1, MV_TF32 = 2, MV_BF16 = 3 };
 bem_status op_matvec(const bem_operator* op, const double* x, double* y, int nrhs, int arith, cudaStream_t s);
+// product workspaces of an operator (made on first use)
+bem_status ensure_ws(const bem_operator* op, int64_t floats);
+// grid of a grid-stride elementwise kernel over n items (256 threads per CTA)
+unsigned grid_for(int64_t n);
+// tensor-core product of up to 64 right-hand sides (internal order, [nrhs][n_tet])
+bem_status op_spmm_tc(const bem_operator* op, const double* x, double* y, int nrhs, bool bf16, cudaStream_t s);
+// 1 when a tensor-core product of the operator gave up on a wait (its output is NaN)
+bem_status op_tc_error(const bem_operator* op, int* flag);
+int64_t tc_table_bytes(const bem_operator* op);
 bem_status op_rhs(const bem_operator* op, int kind, int nrhs, const double* d_params, double* d_b, cudaStream_t s);
 // right-hand side rule for arbitrary data (points [n_surf * 4^level * ng^2][4], weights)
 bem_status op_rhs_points(const bem_operator* op, int level, int ng, double* d_pts, double* d_wts, cudaStream_t s);

@@ -9,23 +9,18 @@
 //   MV_FP64  FP64 accumulation of FP64 values (or of FP32 values when the
 //            operator keeps FP32 values only) - residuals, FP64 solves;
 //   MV_FP32  FP32 values, x rounded to FP32, FP32 accumulation - inner solves;
-//   MV_TF32  tensor-core SpMM: FP32 values and x rounded to TF32 (10-bit
-//            mantissa), FP32 accumulation (mma m16n8k8);
-//   MV_BF16  tensor-core SpMM on a BF16 copy of the values, x in BF16, FP32
-//            accumulation (mma m16n8k16).
-// The tensor-core path treats every 16-row strip of a block as a dense
-// 16 x K tile over the union of its rows' bands (K rounded up to the MMA
-// depth) and multiplies it with the K x nrhs slab of x; each stored value is
-// read from HBM once per product, whatever the number of right-hand sides.
+//   MV_TF32  tensor-core product (tcgen05, stbem_spmm_tc.cu): FP32 values
+//            and x rounded to TF32 (10-bit mantissa), FP32 accumulation;
+//   MV_BF16  the same on a BF16 copy of the values, x in BF16.
+// The tensor-core path treats every block as a dense (rows of I) x K tile
+// over the union of its rows' bands and multiplies it with the K x nrhs slab
+// of x; each stored value is read from HBM once per 64 right-hand sides.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <climits>
 #include <type_traits>
-#include <map>
-#include <mutex>
-#include <tuple>
 #include <vector>
 
 #include "stbem_internal.h"
@@ -148,214 +143,6 @@ __global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out,
     out[i] = (float)in[i];
 }
 
-template <typename V>
-__global__ void k_to_bf16(const V* __restrict__ in, uint16_t* __restrict__ out, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = __bfloat16_as_ushort(__float2bfloat16_rn((float)in[i]));
-}
-
-// ---------------------------------------------------------------------------
-// Tensor-core SpMM
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t to_tf32(float f) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
-  return r;
-}
-
-__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// Packed x for the B fragments: lane (g = lane/4) of an n-tile q needs
-// x[k][8q + g]; the NT8 values of all n-tiles for one k sit together.
-//   TF32: Xp[j][g * NT8 + q] = tf32(x[8q + g][j])
-//   BF16: Xp[p][g * NT8 + q] = bf16(x[8q + g][2p]) | bf16(x[8q + g][2p + 1]) << 16
-template <bool BF16>
-__global__ void k_pack_x(const double* __restrict__ x, int64_t n_tet, int nrhs, int NT8, uint32_t* __restrict__ Xp,
-                         int64_t n_rows) {
-  const int NRp = NT8 * 8;
-  const int64_t total = n_rows * NRp;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = i / NRp;
-    const int slot = (int)(i % NRp);
-    const int g = slot / NT8, q = slot % NT8;
-    const int rh = 8 * q + g;
-    uint32_t v = 0;
-    if (rh < nrhs) {
-      if (BF16) {
-        const int64_t j0 = 2 * row, j1 = 2 * row + 1;
-        float f0 = j0 < n_tet ? (float)x[(int64_t)rh * n_tet + j0] : 0.f;
-        float f1 = j1 < n_tet ? (float)x[(int64_t)rh * n_tet + j1] : 0.f;
-        v = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f0)) |
-            ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f1)) << 16);
-      } else {
-        v = to_tf32((float)x[(int64_t)rh * n_tet + row]);
-      }
-    }
-    Xp[i] = v;
-  }
-}
-
-__global__ void k_unpack_y(const float* __restrict__ Y, int NRp, int64_t n_tet, int nrhs, double* __restrict__ y) {
-  const int64_t total = n_tet * nrhs;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t rh = i / n_tet, j = i % n_tet;
-    y[i] = (double)Y[j * NRp + rh];
-  }
-}
-
-struct SpmmArgs {
-  int64_t n_col;
-  const int32_t* ctb;
-  const int32_t* bw;
-  const int64_t* boff;
-  const int64_t* rsoff;
-  const int32_t* rs;
-  const void* val;      // float (TF32 path) or BF16 bits
-  const uint32_t* X;    // packed x
-  float* Y;             // [n_tet][8 NT8]
-  int strips;           // ceil(max rows per column / 16)
-};
-
-template <int NT8>
-__device__ __forceinline__ void load_b(const uint32_t* p, uint32_t (&b)[NT8]) {
-  if constexpr (NT8 % 4 == 0) {
-#pragma unroll
-    for (int q = 0; q < NT8; q += 4) {
-      uint4 v = __ldg(reinterpret_cast<const uint4*>(p + q));
-      b[q] = v.x; b[q + 1] = v.y; b[q + 2] = v.z; b[q + 3] = v.w;
-    }
-  } else if constexpr (NT8 == 2) {
-    uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
-    b[0] = v.x; b[1] = v.y;
-  } else {
-#pragma unroll
-    for (int q = 0; q < NT8; ++q) b[q] = __ldg(p + q);
-  }
-}
-
-// One CTA per test column I: warp (strip, ws) owns rows 16 strip .. +15 and
-// the trial columns J = ws, ws + WS, ...; the WS partial tiles of a strip are
-// summed in a fixed order at the end.
-template <bool BF16, int NT8, int WS>
-__global__ void __launch_bounds__(512) k_spmm(SpmmArgs a) {
-  extern __shared__ float sred[];
-  constexpr int NRp = NT8 * 8;
-  const int64_t I = blockIdx.x;
-  const int t0 = a.ctb[I], nt = a.ctb[I + 1] - t0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int strip = warp % a.strips, ws = warp / a.strips;
-  const int g = lane >> 2, t = lane & 3;
-  const int r0 = strip * 16 + g, r1 = r0 + 8;
-  const bool v0 = r0 < nt, v1 = r1 < nt;
-  const bool any_rows = strip * 16 < nt;
-  float acc[NT8][4];
-#pragma unroll
-  for (int q = 0; q < NT8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
-  if (any_rows) {
-    for (int64_t J = ws; J < a.n_col; J += WS) {
-      const int64_t b = I * a.n_col + J;
-      const int W = a.bw[b];
-      if (W == 0) continue;
-      const int64_t vo = a.boff[b], ro = a.rsoff[b];
-      const int je = a.ctb[J + 1];
-      const int s0 = v0 ? a.rs[ro + r0] : INT_MAX;
-      const int s1 = v1 ? a.rs[ro + r1] : INT_MAX;
-      int smin = min(s0, s1);
-      int smax = max(v0 ? s0 : INT_MIN, v1 ? s1 : INT_MIN);
-#pragma unroll
-      for (int o = 16; o >= 4; o >>= 1) {
-        smin = min(smin, __shfl_xor_sync(0xffffffffu, smin, o));
-        smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-      }
-      int c0 = smin;
-      if (BF16) c0 &= ~1;
-      const int K = smax + W - c0;
-      if (!BF16) {
-        const float* val = static_cast<const float*>(a.val) + vo;
-        auto ld = [&](bool v, int r, int s, int c) -> uint32_t {
-          const int w = c - s;
-          return (v && w >= 0 && w < W && c < je) ? to_tf32(__ldg(val + (int64_t)w * nt + r)) : 0u;
-        };
-        for (int k0 = 0; k0 < K; k0 += 8) {
-          const int ca = c0 + k0 + t, cb = ca + 4;
-          const uint32_t A0 = ld(v0, r0, s0, ca), A1 = ld(v1, r1, s1, ca);
-          const uint32_t A2 = ld(v0, r0, s0, cb), A3 = ld(v1, r1, s1, cb);
-          uint32_t B0[NT8], B1[NT8];
-          load_b<NT8>(a.X + (int64_t)min(ca, je - 1) * NRp + g * NT8, B0);
-          load_b<NT8>(a.X + (int64_t)min(cb, je - 1) * NRp + g * NT8, B1);
-#pragma unroll
-          for (int q = 0; q < NT8; ++q) mma_tf32(acc[q], A0, A1, A2, A3, B0[q], B1[q]);
-        }
-      } else {
-        const uint16_t* val = static_cast<const uint16_t*>(a.val) + vo;
-        auto ld = [&](bool v, int r, int s, int c) -> uint32_t {
-          const int w = c - s;
-          return (v && w >= 0 && w < W && c < je) ? (uint32_t)__ldg(val + (int64_t)w * nt + r) : 0u;
-        };
-        const int plast = (je - 1) >> 1;
-        for (int k0 = 0; k0 < K; k0 += 16) {
-          const int pa = c0 + k0 + 2 * t, pb = pa + 8;
-          const uint32_t A0 = ld(v0, r0, s0, pa) | (ld(v0, r0, s0, pa + 1) << 16);
-          const uint32_t A1 = ld(v1, r1, s1, pa) | (ld(v1, r1, s1, pa + 1) << 16);
-          const uint32_t A2 = ld(v0, r0, s0, pb) | (ld(v0, r0, s0, pb + 1) << 16);
-          const uint32_t A3 = ld(v1, r1, s1, pb) | (ld(v1, r1, s1, pb + 1) << 16);
-          uint32_t B0[NT8], B1[NT8];
-          load_b<NT8>(a.X + (int64_t)min(pa >> 1, plast) * NRp + g * NT8, B0);
-          load_b<NT8>(a.X + (int64_t)min(pb >> 1, plast) * NRp + g * NT8, B1);
-#pragma unroll
-          for (int q = 0; q < NT8; ++q) mma_bf16(acc[q], A0, A1, A2, A3, B0[q], B1[q]);
-        }
-      }
-    }
-  }
-  if constexpr (WS > 1) {
-    const int slab = NT8 * 4 * 32;
-    if (ws > 0 && any_rows) {
-      float* dst = sred + (int64_t)((ws - 1) * a.strips + strip) * slab;
-#pragma unroll
-      for (int q = 0; q < NT8; ++q)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) dst[(q * 4 + e) * 32 + lane] = acc[q][e];
-    }
-    __syncthreads();
-    if (ws == 0 && any_rows) {
-      for (int u = 1; u < WS; ++u) {
-        const float* src = sred + (int64_t)((u - 1) * a.strips + strip) * slab;
-#pragma unroll
-        for (int q = 0; q < NT8; ++q)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) acc[q][e] += src[(q * 4 + e) * 32 + lane];
-      }
-    }
-  }
-  if (ws == 0 && any_rows) {
-#pragma unroll
-    for (int q = 0; q < NT8; ++q) {
-      const int col = 8 * q + 2 * t;
-      if (v0) *reinterpret_cast<float2*>(a.Y + (int64_t)(t0 + r0) * NRp + col) = make_float2(acc[q][0], acc[q][1]);
-      if (v1) *reinterpret_cast<float2*>(a.Y + (int64_t)(t0 + r1) * NRp + col) = make_float2(acc[q][2], acc[q][3]);
-    }
-  }
-}
-
-namespace {
-
 unsigned grid_for(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16); }
 
 bem_status ensure_ws(const bem_operator* op, int64_t floats) {
@@ -371,112 +158,6 @@ bem_status ensure_ws(const bem_operator* op, int64_t floats) {
   op->ws_len = floats;
   return BEM_OK;
 }
-
-bem_status ensure_val16(const bem_operator* op, cudaStream_t s) {
-  if (op->d_val16) return BEM_OK;
-  const int64_t n = std::max<int64_t>(op->nstored, 1);
-  if (cudaMalloc(&op->d_val16, sizeof(uint16_t) * n) != cudaSuccess) {
-    cudaGetLastError();
-    op->d_val16 = nullptr;
-    set_error("out of device memory (BF16 values)");
-    return BEM_ERR_OUT_OF_MEMORY;
-  }
-  if (op->nstored > 0) {
-    if (op->d_val32) k_to_bf16<float><<<grid_for(op->nstored), 256, 0, s>>>(op->d_val32, op->d_val16, op->nstored);
-    else k_to_bf16<double><<<grid_for(op->nstored), 256, 0, s>>>(op->d_val, op->d_val16, op->nstored);
-    STBEM_CUDA(cudaGetLastError());
-  }
-  return BEM_OK;
-}
-
-// candidate warps per strip, the tuned choice per shape (process-wide, so
-// that equal shapes always take the same summation order)
-std::mutex g_tune_mu;
-std::map<std::tuple<int64_t, int, int, int, int>, int> g_tuned;
-
-template <bool BF16, int NT8, int WS>
-bem_status launch_spmm_ws(const SpmmArgs& a, cudaStream_t s) {
-  const int threads = a.strips * WS * 32;
-  const size_t smem = WS > 1 ? sizeof(float) * (size_t)(WS - 1) * a.strips * NT8 * 4 * 32 : 0;
-  if (smem > 48 * 1024)
-  {
-      bem_status sa = ensure_smem_attr((const void*)k_spmm<BF16, NT8, WS>, smem);
-      if (sa != BEM_OK) return sa;
-    }
-  k_spmm<BF16, NT8, WS><<<(unsigned)a.n_col, threads, smem, s>>>(a);
-  STBEM_CUDA(cudaGetLastError());
-  return BEM_OK;
-}
-
-template <bool BF16, int NT8>
-bem_status launch_spmm(const SpmmArgs& a, int ws, cudaStream_t s) {
-  switch (ws) {
-    case 1: return launch_spmm_ws<BF16, NT8, 1>(a, s);
-    case 2: return launch_spmm_ws<BF16, NT8, 2>(a, s);
-    case 4: return launch_spmm_ws<BF16, NT8, 4>(a, s);
-    default: return launch_spmm_ws<BF16, NT8, 8>(a, s);
-  }
-}
-
-bool ws_ok(int strips, int nt8, int ws) {
-  return strips * ws <= 16 && (ws == 1 || (size_t)(ws - 1) * strips * nt8 * 4 * 32 * 4 <= 100 * 1024);
-}
-
-template <bool BF16, int NT8>
-bem_status run_spmm(const bem_operator* op, const SpmmArgs& a, cudaStream_t s) {
-  const auto key = std::make_tuple(op->mesh->n_col, op->mesh->max_col_tets, NT8, (int)BF16, op->ctx->device);
-  // candidates differ in summation order: the choice is kept per shape for the process
-  int ws = 0;
-  {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tuned.find(key);
-    if (it != g_tuned.end()) ws = it->second;
-  }
-  if (ws) return launch_spmm<BF16, NT8>(a, ws, s);
-  // autotune: time every admissible candidate once (after one warm-up launch)
-  cudaEvent_t e0, e1;
-  STBEM_CUDA(cudaEventCreate(&e0));
-  STBEM_CUDA(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int best_ws = 1;
-  bem_status st = BEM_OK;
-  for (int c : {1, 2, 4, 8}) {
-    if (!ws_ok(a.strips, NT8, c)) continue;
-    if ((st = launch_spmm<BF16, NT8>(a, c, s)) != BEM_OK) break;
-    cudaEventRecord(e0, s);
-    if ((st = launch_spmm<BF16, NT8>(a, c, s)) != BEM_OK) break;
-    cudaEventRecord(e1, s);
-    cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) { best = ms; best_ws = c; }
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (st != BEM_OK) return st;
-  if (best >= 1e30f) {
-    set_error("tensor-core product: no launch shape fits this operator");
-    return BEM_ERR_UNSUPPORTED;
-  }
-  {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tuned[key] = best_ws;
-  }
-  // the result of the chosen variant (the candidates differ in summation order)
-  return launch_spmm<BF16, NT8>(a, best_ws, s);
-}
-
-template <bool BF16>
-bem_status spmm_nt8(const bem_operator* op, const SpmmArgs& a, int nt8, cudaStream_t s) {
-  switch (nt8) {
-    case 1: return run_spmm<BF16, 1>(op, a, s);
-    case 2: return run_spmm<BF16, 2>(op, a, s);
-    case 4: return run_spmm<BF16, 4>(op, a, s);
-    default: return run_spmm<BF16, 8>(op, a, s);
-  }
-}
-
-}  // namespace
 
 // NR right-hand sides per pass over the values (1: the single-vector kernel,
 // with fewer registers)
@@ -518,45 +199,11 @@ bem_status op_matvec(const bem_operator* op, const double* x, double* y, int nrh
   const bem_mesh* m = op->mesh;
   const int64_t n = m->n_tet;
   if (arith == MV_TF32 || arith == MV_BF16) {
-    // groups of up to 64 right-hand sides
+    // passes of up to 64 right-hand sides
     for (int r0 = 0; r0 < nrhs; r0 += 64) {
       const int nr = std::min(64, nrhs - r0);
-      const int nt8 = nr <= 8 ? 1 : nr <= 16 ? 2 : nr <= 32 ? 4 : 8;
-      const int NRp = nt8 * 8;
-      const bool bf16 = arith == MV_BF16;
-      const float* vals32 = op->d_val32;
-      if (!bf16 && !vals32) {
-        set_error("TF32 products need FP32 values (store_fp32 = 1)");
-        return BEM_ERR_INVALID_ARG;
-      }
-      if (bf16) {
-        bem_status st = ensure_val16(op, s);
-        if (st != BEM_OK) return st;
-      }
-      const int64_t xrows = bf16 ? (n + 1) / 2 : n;
-      bem_status st = ensure_ws(op, xrows * NRp + n * NRp);
+      const bem_status st = op_spmm_tc(op, x + (int64_t)r0 * n, y + (int64_t)r0 * n, nr, arith == MV_BF16, s);
       if (st != BEM_OK) return st;
-      uint32_t* Xp = reinterpret_cast<uint32_t*>(op->d_ws);
-      float* Yp = op->d_ws + xrows * NRp;
-      const double* xr = x + (int64_t)r0 * n;
-      if (bf16) k_pack_x<true><<<grid_for(xrows * NRp), 256, 0, s>>>(xr, n, nr, nt8, Xp, xrows);
-      else k_pack_x<false><<<grid_for(xrows * NRp), 256, 0, s>>>(xr, n, nr, nt8, Xp, xrows);
-      STBEM_CUDA(cudaGetLastError());
-      SpmmArgs a;
-      a.n_col = m->n_col;
-      a.ctb = m->d_col_tet_begin;
-      a.bw = op->d_bw;
-      a.boff = op->d_boff;
-      a.rsoff = op->d_rsoff;
-      a.rs = op->d_rs;
-      a.val = bf16 ? (const void*)op->d_val16 : (const void*)vals32;
-      a.X = Xp;
-      a.Y = Yp;
-      a.strips = (m->max_col_tets + 15) / 16;
-      st = bf16 ? spmm_nt8<true>(op, a, nt8, s) : spmm_nt8<false>(op, a, nt8, s);
-      if (st != BEM_OK) return st;
-      k_unpack_y<<<grid_for(n * nr), 256, 0, s>>>(Yp, NRp, n, nr, y + (int64_t)r0 * n);
-      STBEM_CUDA(cudaGetLastError());
     }
     return BEM_OK;
   }

@@ -14,6 +14,7 @@
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <set>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -108,7 +109,7 @@ struct bem_server {
   std::vector<bem_context*> slot_ctx;
   std::vector<std::thread> workers;
   std::mutex mu;
-  std::condition_variable cv_work, cv_mem, cv_done;
+  std::condition_variable cv_work, cv_mem, cv_done, cv_cache;
   std::deque<std::unique_ptr<Job>> queue;
   std::deque<uint64_t> mem_fifo;              // requests waiting for a reservation, in order
   std::deque<std::unique_ptr<Done>> ready;    // completed, not yet polled
@@ -123,6 +124,7 @@ struct bem_server {
   std::vector<double> lat;
   // resident operators (cache_operators = 1)
   std::vector<std::unique_ptr<CacheEntry>> cache;
+  std::set<uint64_t> building;   // meshes whose operator a slot is assembling now
   uint64_t use_clock = 0;
   int64_t cache_hits = 0, cached_bytes = 0;
 };
@@ -189,7 +191,9 @@ int64_t admission_bytes(const bem_operator* op, const bem_server_opts& o, int nr
   if (o.inner_dtype == BEM_DTYPE_TF32 || o.inner_dtype == BEM_DTYPE_BF16)
     b += (n + 1) * (int64_t)std::min(nrhs, 64) * 8 * 2;
   if (o.inner_dtype == BEM_DTYPE_FP32) b += n * (int64_t)nrhs * 4;
-  if (o.inner_dtype == BEM_DTYPE_BF16) b += op->nstored * 2;
+  // chunk slots of the tensor-core product: at most two 16-byte slots per block row beyond the values
+  if (o.inner_dtype == BEM_DTYPE_TF32) b += op->nstored * 4 + op->nrows_stored * 32;
+  if (o.inner_dtype == BEM_DTYPE_BF16) b += op->nstored * 2 + op->nrows_stored * 32;
   return b;
 }
 
@@ -241,18 +245,48 @@ bem_status run_job(bem_server* S, bem_context* cx, const Job& J, Done& D, int64_
   const int nrhs = J.nrhs;
   const bool caching = S->o.cache_operators != 0;
   const uint64_t key = caching ? job_key(J) : 0;
-  // a resident operator on the same mesh
+  // a resident operator on the same mesh; a request whose mesh is in use by
+  // another request, or being assembled by one, waits for it instead of
+  // assembling a second copy
   CacheEntry* hit = nullptr;
+  bool builder = false;
   if (caching) {
-    std::lock_guard<std::mutex> lk(S->mu);
-    for (auto& e : S->cache)
-      if (e->key == key && !e->busy && same_mesh(*e, J)) {
-        e->busy = true;
-        e->last = ++S->use_clock;
-        hit = e.get();
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+      bool present = false;
+      for (auto& e : S->cache)
+        if (e->key == key && same_mesh(*e, J)) {
+          present = true;
+          if (!e->busy) {
+            e->busy = true;
+            e->last = ++S->use_clock;
+            hit = e.get();
+          }
+          break;
+        }
+      if (hit) break;
+      if (!present && !S->building.count(key)) {
+        S->building.insert(key);
+        builder = true;
         break;
       }
+      S->cv_cache.wait(lk);
+    }
   }
+  // the assembling request clears its mark on every way out (after keeping the operator)
+  struct BuildMark {
+    bem_server* S;
+    uint64_t key;
+    bool on;
+    ~BuildMark() {
+      if (!on) return;
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->building.erase(key);
+      }
+      S->cv_cache.notify_all();
+    }
+  } mark{S, key, builder};
   if (hit) {
     const int64_t need = admission_bytes(hit->op, S->o, nrhs) - operator_value_bytes(hit->op);
     bem_status st = acquire(S, J.ticket, need);
@@ -267,6 +301,7 @@ bem_status run_job(bem_server* S, bem_context* cx, const Job& J, Done& D, int64_
       if (st == BEM_OK || st == BEM_ERR_NOT_CONVERGED) ++S->cache_hits;
     }
     S->cv_mem.notify_all();
+    S->cv_cache.notify_all();
     D.c.cache_hit = 1;
     return st;
   }
@@ -306,7 +341,7 @@ bem_status run_job(bem_server* S, bem_context* cx, const Job& J, Done& D, int64_
   }
   // keep the operator resident if the pool has room for it beside the others
   const int64_t keep = operator_value_bytes(op) + sbytes + op->ws_len * (int64_t)sizeof(float) +
-                       op->pv_len * (int64_t)sizeof(double) + (op->d_val16 ? op->nstored * 2 : 0);
+                       op->pv_len * (int64_t)sizeof(double) + tc_table_bytes(op);
   bool kept = false;
   {
     std::lock_guard<std::mutex> lk(S->mu);
@@ -412,6 +447,8 @@ bem_status bem_server_create(bem_context* ctx, const bem_server_opts* opts, bem_
       for (auto* q : S->slot_ctx) bem_context_destroy(q);
       return st;
     }
+    c->tune_mode = ctx->tune_mode;   // slots assemble with the server context's tuning
+    c->tune_path = ctx->tune_path;
     S->slot_ctx.push_back(c);
   }
   for (int k = 0; k < o.max_slots; ++k) S->workers.emplace_back(worker, S.get(), k);

@@ -123,3 +123,17 @@ def test_matrix_free_product_matches_assembled(ctx, precision, tol):
     wf, infof = mf.solve(b, tol=1e-10, restart=50, maxit=1000)
     assert infof[0]["converged"]
     assert np.abs(wf - w).max() <= 1e-8 * np.abs(w).max()
+
+
+def test_bounded_wait_gives_up_and_leaves_the_context_usable(ctx, small):
+    """The tensor-core product's mbarrier waits are bounded: a wait on a
+    barrier that nothing completes returns after its budget with
+    BEM_ERR_DEVICE_TIMEOUT (the product then flags the operator), and the
+    context runs products afterwards."""
+    st, ms = ctx.selftest_bounded_wait()
+    assert st == 5 and 0.0 < ms < 1000.0
+    m, op, A = small
+    x = np.random.default_rng(0).normal(size=(4, m.n_tet))
+    y = op.matvec(torch.tensor(x, device="cuda"), dtype="bf16").cpu().numpy()
+    assert np.all(np.isfinite(y))
+    assert op.check()[0] == 0          # no product of this operator gave up
