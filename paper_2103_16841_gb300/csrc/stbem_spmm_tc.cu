@@ -13,8 +13,9 @@
 // kc of row m at kc * (rows * 16) + m * 16, i.e. core matrices of 8 rows x
 // 16 bytes, K-adjacent core matrices rows * 16 bytes apart (leading byte
 // offset), M/N-adjacent ones 128 bytes apart (stride byte offset).
-//   X is packed per pass as Xc[chunk][rhs][16 bytes], so the TMA box
-//   {16 bytes, N, 2 chunks} lands in exactly this layout.
+//   X is packed per pass as Xc[chunk][rhs][16 bytes]; one chunk is N x 16
+//   contiguous bytes, and a TMA box of {256-byte rows, N / 16 rows, 2
+//   chunks} (one K step) lands in exactly this layout.
 //   The values are kept, for this product, in the same chunks: row r's band
 //   re-cut at the 16-byte chunk boundaries of the trial panel index (slot j
 //   of row r = the chunk starting at panel E * (floor(rs[r] / E) + j), zeros
@@ -25,16 +26,20 @@
 // One CTA per test column I, six warps:
 //   warps 0-3  build the A tile of each block (thread = row: its slots to
 //              their chunk positions, the previous band's other chunks
-//              cleared), then read the accumulator rows out of tensor memory
-//              (thread = row) into y;
+//              cleared) in shared memory (k_spmm_tc) or in tensor memory with
+//              tcgen05.st (k_spmm_tm; the MMA then reads A from tensor
+//              memory, and shared memory holds only B, slots and row starts,
+//              so more stages fit), then read the accumulator rows out of
+//              tensor memory (thread = row) into y;
 //   warp 4     (one lane) loads, per block, the X rows (TMA tensor copies),
 //              the value slots and the row starts (bulk copies) and the
-//              block's record, into one of up to 4 pipeline stages;
+//              block's record, into one of up to 6 pipeline stages;
 //   warp 5     owns the tensor-memory allocation; one lane issues
 //              tcgen05.mma (M = 128 rows, N = right-hand sides rounded up to
 //              16, K = 16 BF16 or 8 TF32 per instruction) accumulating every
 //              block of the column into one tensor-memory tile, and commits
 //              each stage back to the builders and the loader.
+// Which kernel and how many stages (1-6) run is timed once per shape.
 // Every mbarrier wait is bounded (kWaitBudget); a wait that runs out flags
 // the operator, stops the CTA's pipeline and writes NaN to its rows.
 #include <cuda.h>
@@ -78,7 +83,7 @@ namespace {
 
 constexpr long long kWaitBudget = 4000000000LL;   // clock cycles (about 2 s) per wait
 constexpr int kThreads = 192;
-constexpr int kMaxStages = 4;
+constexpr int kMaxStages = 6;
 constexpr uint32_t kRsBytes = 1024;   // per stage: row starts (<= 784 bytes) and the block record
 constexpr uint32_t kMetaOff = 896;
 
@@ -401,8 +406,208 @@ __global__ void __launch_bounds__(kThreads, 1) k_spmm_tc(const TcArgs a, const _
   }
 }
 
+// The same product with the A tiles in tensor memory: per stage MT x nkc
+// chunks of 4 columns each (row m = lane m), written by the builder warps
+// with tcgen05.st (warp w owns lanes 32w..32w+31, i.e. rows 32w + lane) and
+// read by the MMA straight from tensor memory; shared memory then holds only
+// the B tiles, value slots and row starts, so more stages fit.
+template <bool TF32, int MT>
+__global__ void __launch_bounds__(kThreads, 1) k_spmm_tm(const TcArgs a, const __grid_constant__ CUtensorMap tmx) {
+  using namespace tc;
+  constexpr int E = TF32 ? 4 : 8;         // elements per 16-byte chunk
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t I = blockIdx.x;
+  const int t0 = a.ctb[I], nt = a.ctb[I + 1] - t0;
+  const int b0 = a.colptr[I], nb = a.colptr[I + 1] - b0;
+  const int ST = a.stages, N = a.N, NKC = a.nkc;
+  const uint32_t b_bytes = (uint32_t)NKC * N * 16;
+  const uint32_t stage_bytes = b_bytes + a.v_bytes + kRsBytes;
+  unsigned char* bar_base = smem + (size_t)ST * stage_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(bar_base);   // full_a[ST], full_b[ST], empty[ST], done
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar_base + 8 * (3 * ST + 1));
+  volatile int* abort_flag = reinterpret_cast<int*>(bar_base + 8 * (3 * ST + 1) + 4);
+  auto full_a = [&](int s) { return smem_u32(&bars[s]); };
+  auto full_b = [&](int s) { return smem_u32(&bars[ST + s]); };
+  auto empty = [&](int s) { return smem_u32(&bars[2 * ST + s]); };
+  const uint32_t done = smem_u32(&bars[3 * ST]);
+  auto stage_b = [&](int s) { return smem + (size_t)s * stage_bytes; };
+  auto stage_v = [&](int s) { return smem + (size_t)s * stage_bytes + b_bytes; };
+  auto stage_r = [&](int s) { return smem + (size_t)s * stage_bytes + b_bytes + a.v_bytes; };
+  auto meta = [&](int s) { return reinterpret_cast<TcBlk*>(stage_r(s) + kMetaOff); };
+  auto fail = [&]() {
+    *abort_flag = 1;
+    atomicExch(a.err, 1);
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(full_a(s), 128);
+      mbar_init(full_b(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    fence_proxy_async();
+  }
+  if (warp == 5) tmem_alloc(smem_u32(slot), a.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  // column of chunk kc of M-tile mt in stage s (after the MT x N accumulator columns)
+  auto a_col = [&](int s, int mt, int kc) { return (uint32_t)(MT * N + ((s * MT + mt) * NKC + kc) * 4); };
+
+  if (warp < 4) {
+    const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+    // the A tiles start zero
+    for (int s = 0; s < ST; ++s)
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt)
+        for (int kc = 0; kc < NKC; ++kc) tmem_st4(tmem + lanes + a_col(s, mt, kc), make_uint4(0, 0, 0, 0));
+    tmem_st_wait();
+    // ---------------------------------------------------------------- builders
+    int dlo[kMaxStages][MT], dhi[kMaxStages][MT];   // chunks of each stage this warp left non-zero
+#pragma unroll
+    for (int q = 0; q < kMaxStages; ++q)
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) dlo[q][mt] = dhi[q][mt] = 0;
+    for (int k = 0; k < nb; ++k) {
+      const int s = k % ST, u = k / ST;
+      if (u > 0 && !mbar_wait(empty(s), (u - 1) & 1, kWaitBudget)) { fail(); break; }
+      if (!mbar_wait(full_b(s), u & 1, kWaitBudget)) { fail(); break; }   // record, values, row starts landed
+      if (*abort_flag) break;
+      const TcBlk* bm = meta(s);
+      const int c0c = bm->cmin / E;
+      const int nkk = 2 * ((bm->cend - c0c * E + 2 * E - 1) / (2 * E));   // chunks the MMAs read
+      const int S = tc_slots(bm->W, E);
+      const int32_t* R = reinterpret_cast<const int32_t*>(stage_r(s)) + (int)(bm->ro & 3);
+      const uint4* V = reinterpret_cast<const uint4*>(stage_v(s));
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        const int r = mt * 128 + warp * 32 + lane;
+        int lo = 0, hi = 0;
+        if (r < nt) {
+          lo = R[r] / E - c0c;
+          hi = min(lo + S, nkk);
+        }
+        // the warp's range: its rows' bands and what it left non-zero in this stage
+        int wlo = hi > lo ? lo : INT_MAX, whi = hi > lo ? hi : 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          wlo = min(wlo, __shfl_xor_sync(0xffffffffu, wlo, o));
+          whi = max(whi, __shfl_xor_sync(0xffffffffu, whi, o));
+        }
+        int olo = 0, ohi = 0;
+#pragma unroll
+        for (int q = 0; q < kMaxStages; ++q)
+          if (q == s) { olo = dlo[q][mt]; ohi = dhi[q][mt]; }
+        const int from = whi > 0 ? min(wlo, ohi > olo ? olo : wlo) : olo;
+        const int to = max(whi, ohi);
+        for (int kc = from; kc < to; ++kc) {
+          const uint4 v = (kc >= lo && kc < hi) ? V[(kc - lo) * nt + r] : make_uint4(0, 0, 0, 0);
+          tmem_st4(tmem + lanes + a_col(s, mt, kc), v);
+        }
+#pragma unroll
+        for (int q = 0; q < kMaxStages; ++q)
+          if (q == s) { dlo[q][mt] = whi > 0 ? wlo : 0; dhi[q][mt] = whi; }
+      }
+      tmem_st_wait();
+      tc_fence_before();
+      mbar_arrive(full_a(s));
+    }
+    // ---------------------------------------------------------------- epilogue
+    __syncwarp();
+    const bool ok = mbar_wait(done, 0, kWaitBudget);
+    if (!ok) fail();
+    tc_fence_after();
+    const bool bad = !ok || *abort_flag;
+    __syncwarp();
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+      const int r = mt * 128 + warp * 32 + lane;
+      for (int c = 0; c < N; c += 16) {
+        float v[16];
+        tmem_ld16(tmem + lanes + (uint32_t)(mt * N + c), v);
+        if (r < nt) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = c + j;
+            if (n < a.nr) {
+              const double o = nb == 0 ? 0.0 : bad ? __longlong_as_double(0x7ff8000000000000LL) : (double)v[j];
+              a.y[(int64_t)n * a.n_tet + t0 + r] = o;
+            }
+          }
+        }
+      }
+    }
+  } else if (warp == 4) {
+    // ---------------------------------------------------------------- loader
+    if (lane == 0) {
+      prefetch_tensormap(&tmx);
+      int issued = 0;
+      TcBlk nxt = nb > 0 ? a.blk[b0] : TcBlk{};
+      for (int k = 0; k < nb; ++k) {
+        const int s = k % ST, u = k / ST;
+        const TcBlk b = nxt;
+        if (k + 1 < nb) nxt = a.blk[b0 + k + 1];          // the next record in flight meanwhile
+        if (u > 0 && !mbar_wait(empty(s), (u - 1) & 1, kWaitBudget)) { fail(); break; }
+        if (*abort_flag) break;
+        *meta(s) = b;
+        const int c0c = b.cmin / E;
+        const int nk = (b.cend - c0c * E + 2 * E - 1) / (2 * E);
+        const uint32_t v_bytes = (uint32_t)tc_slots(b.W, E) * nt * 16;
+        const uint64_t rs_src = reinterpret_cast<uint64_t>(a.rs + (b.ro & ~(int64_t)3));
+        const uint32_t rs_bytes = (uint32_t)(((b.ro & 3) + nt + 3) & ~3) * 4;
+        mbar_arrive_expect_tx(full_b(s), (uint32_t)nk * 2 * N * 16 + v_bytes + rs_bytes);
+        const uint32_t B = smem_u32(stage_b(s));
+        for (int ks = 0; ks < nk; ++ks)
+          tma_load_3d(B + (uint32_t)ks * 2 * N * 16, &tmx, 0, 0, c0c + 2 * ks, full_b(s));
+        bulk_load(smem_u32(stage_v(s)), reinterpret_cast<uint64_t>(a.vals + b.vc[TF32 ? 1 : 0]), v_bytes, full_b(s));
+        bulk_load(smem_u32(stage_r(s)), rs_src, rs_bytes, full_b(s));
+        issued = k + 1;
+      }
+      // copies still in flight land before the CTA's shared memory is released
+      for (int k = max(0, issued - ST); k < issued; ++k)
+        if (!mbar_wait(full_b(k % ST), (k / ST) & 1, kWaitBudget)) fail();
+    }
+  } else {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(TF32 ? 2u : 1u, 128, N);
+      for (int k = 0; k < nb; ++k) {
+        const int s = k % ST, u = k / ST;
+        if (!mbar_wait(full_a(s), u & 1, kWaitBudget) || !mbar_wait(full_b(s), u & 1, kWaitBudget)) {
+          fail();
+          break;
+        }
+        if (*abort_flag) break;
+        tc_fence_after();
+        const TcBlk* bm = meta(s);
+        const int c0c = bm->cmin / E;
+        const int nk = (bm->cend - c0c * E + 2 * E - 1) / (2 * E);
+        const uint32_t B = smem_u32(stage_b(s));
+        for (int ks = 0; ks < nk; ++ks) {
+          const uint64_t bd = smem_desc(B + (uint32_t)ks * 2 * N * 16, (uint32_t)N * 16, 128);
+#pragma unroll
+          for (int mt = 0; mt < MT; ++mt)
+            mma_ts<TF32>(tmem + (uint32_t)(mt * N), tmem + a_col(s, mt, 2 * ks), bd, idesc, (k > 0 || ks > 0) ? 1u : 0u);
+        }
+        mma_commit(empty(s));
+      }
+      mma_commit(done);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 5) {
+    tc_fence_after();
+    tmem_dealloc(tmem, a.tmem_cols);
+  }
+}
+
 std::mutex g_tc_mu;
-std::map<std::tuple<int64_t, int, int, int64_t, int, int, int>, int> g_tc_stages;   // shape -> pipeline stages
+std::map<std::tuple<int64_t, int, int, int64_t, int, int, int>, std::pair<int, int>> g_tc_shape;   // shape -> (kind, stages)
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static std::once_flag once;
@@ -530,10 +735,13 @@ bem_status ensure_tc_vals(const bem_operator* op, bool tf32, cudaStream_t s) {
   return BEM_OK;
 }
 
+// kind 0: A tiles in shared memory (k_spmm_tc); kind 1: in tensor memory (k_spmm_tm)
 template <bool TF32, int MT>
-bem_status launch_tc(const TcArgs& a, const CUtensorMap& map, size_t smem, int64_t n_col, cudaStream_t s) {
-  TRY_STATUS(ensure_smem_attr((const void*)k_spmm_tc<TF32, MT>, smem));
-  k_spmm_tc<TF32, MT><<<(unsigned)n_col, kThreads, smem, s>>>(a, map);
+bem_status launch_tc(int kind, const TcArgs& a, const CUtensorMap& map, size_t smem, int64_t n_col, cudaStream_t s) {
+  const void* kern = kind ? (const void*)k_spmm_tm<TF32, MT> : (const void*)k_spmm_tc<TF32, MT>;
+  TRY_STATUS(ensure_smem_attr(kern, smem));
+  if (kind) k_spmm_tm<TF32, MT><<<(unsigned)n_col, kThreads, smem, s>>>(a, map);
+  else k_spmm_tc<TF32, MT><<<(unsigned)n_col, kThreads, smem, s>>>(a, map);
   STBEM_CUDA(cudaGetLastError());
   return BEM_OK;
 }
@@ -574,14 +782,17 @@ bem_status op_spmm_tc(const bem_operator* op, const double* x, double* y, int nr
   else k_pack_xc<true><<<grid_for(nchunks * N * E), 256, 0, s>>>(x, n, nrhs, N, nchunks, Xc);
   STBEM_CUDA(cudaGetLastError());
 
+  // Xc as rows of 256 bytes: {256-byte row, N / 16 rows per chunk, chunks};
+  // a box of {256 bytes, N / 16, 2 chunks} is one K step of the B tile
   CUtensorMap map;
-  cuuint64_t dims[3] = {(cuuint64_t)E, (cuuint64_t)N, (cuuint64_t)nchunks};
-  cuuint64_t strides[2] = {16, (cuuint64_t)N * 16};
-  cuuint32_t box[3] = {(cuuint32_t)E, (cuuint32_t)N, 2};
+  const int inner = 256 / (bf16 ? 2 : 4);
+  cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)(N / 16), (cuuint64_t)nchunks};
+  cuuint64_t strides[2] = {256, (cuuint64_t)N * 16};
+  cuuint32_t box[3] = {(cuuint32_t)inner, (cuuint32_t)(N / 16), 2};
   cuuint32_t es[3] = {1, 1, 1};
   const CUresult r = enc(&map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, Xc, dims,
                          strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("tensor-core product: tensor map rejected (" + std::to_string((int)r) + ")");
     return BEM_ERR_CUDA;
@@ -592,7 +803,9 @@ bem_status op_spmm_tc(const bem_operator* op, const double* x, double* y, int nr
   // value slots of the largest block; a multiple of 1024 bytes keeps every
   // stage's TMA tiles aligned
   const size_t v_bytes = ((size_t)op->tcv_cap[bf16 ? 0 : 1] + 1023) & ~(size_t)1023;
-  const size_t stage = (size_t)nkc * (MT * 128 + N) * 16 + v_bytes + kRsBytes;
+  // shared memory per stage: A tile (kind 0 only), B tile, value slots, row starts
+  const size_t stage_b = (size_t)nkc * N * 16 + v_bytes + kRsBytes;
+  const size_t stage_a = (size_t)nkc * MT * 128 * 16;
   const size_t tail = 128;   // mbarriers, tensor-memory address, abort flag
   size_t smem_max = 0;
   {
@@ -600,10 +813,6 @@ bem_status op_spmm_tc(const bem_operator* op, const double* x, double* y, int nr
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     smem_max = (size_t)v;
-  }
-  if (stage + tail > smem_max) {
-    set_error("tensor-core product: the widest block does not fit in shared memory");
-    return BEM_ERR_UNSUPPORTED;
   }
   TcArgs a;
   a.ctb = m->d_col_tet_begin;
@@ -617,41 +826,57 @@ bem_status op_spmm_tc(const bem_operator* op, const double* x, double* y, int nr
   a.N = N;
   a.nkc = nkc;
   a.v_bytes = (uint32_t)v_bytes;
-  uint32_t cols = 32;
-  while (cols < (uint32_t)(MT * N)) cols <<= 1;
-  a.tmem_cols = cols;
   a.err = op->d_tc_err;
-  auto launch = [&](int stages) -> bem_status {
-    a.stages = stages;
-    const size_t smem = stages * stage + tail;
-    if (bf16)
-      return MT == 1 ? launch_tc<false, 1>(a, map, smem, m->n_col, s) : launch_tc<false, 2>(a, map, smem, m->n_col, s);
-    return MT == 1 ? launch_tc<true, 1>(a, map, smem, m->n_col, s) : launch_tc<true, 2>(a, map, smem, m->n_col, s);
+  auto pow2 = [](int c) {
+    uint32_t v = 32;
+    while (v < (uint32_t)c) v <<= 1;
+    return v;
   };
-  // pipeline depth (1 to 4 stages; with the stage size it fixes the CTAs per
-  // SM): timed once per shape in the process, then kept. The stages do not
-  // change the arithmetic (every CTA sums its blocks in order), so the
-  // candidates give the same bits.
-  const int max_st = (int)std::min<size_t>(kMaxStages, (smem_max - tail) / stage);
+  // tensor-memory columns: the accumulator, and for kind 1 the A tiles of every stage
+  auto cols_of = [&](int kind, int st) { return kind ? MT * N + st * MT * nkc * 4 : MT * N; };
+  auto fits = [&](int kind, int st) {
+    const size_t smem = st * (stage_b + (kind ? 0 : stage_a)) + tail;
+    return smem <= smem_max && cols_of(kind, st) <= 512;
+  };
+  auto launch = [&](int kind, int st) -> bem_status {
+    a.stages = st;
+    a.tmem_cols = pow2(cols_of(kind, st));
+    const size_t smem = st * (stage_b + (kind ? 0 : stage_a)) + tail;
+    if (bf16)
+      return MT == 1 ? launch_tc<false, 1>(kind, a, map, smem, m->n_col, s)
+                     : launch_tc<false, 2>(kind, a, map, smem, m->n_col, s);
+    return MT == 1 ? launch_tc<true, 1>(kind, a, map, smem, m->n_col, s)
+                   : launch_tc<true, 2>(kind, a, map, smem, m->n_col, s);
+  };
+  // launch shape: where the A tiles live and the pipeline depth (1 to 6
+  // stages; with the stage size they fix the CTAs per SM), timed once per
+  // shape in the process, then kept. Neither changes the arithmetic (every
+  // CTA sums its blocks in order), so the candidates give the same bits.
+  std::vector<std::pair<int, int>> cand;
+  for (int kind = 0; kind < 2; ++kind)
+    for (int st = 1; st <= kMaxStages; ++st)
+      if (fits(kind, st)) cand.emplace_back(kind, st);
+  if (cand.empty()) {
+    set_error("tensor-core product: the widest block does not fit in shared or tensor memory");
+    return BEM_ERR_UNSUPPORTED;
+  }
   const auto key = std::make_tuple(m->n_col, m->max_col_tets, op->tc_span[bf16 ? 0 : 1], op->tcv_cap[bf16 ? 0 : 1], N,
                                    (int)bf16, op->ctx->device);
-  int stages = 0;
   {
     std::lock_guard<std::mutex> lk(g_tc_mu);
-    auto it = g_tc_stages.find(key);
-    if (it != g_tc_stages.end()) stages = it->second;
+    auto it = g_tc_shape.find(key);
+    if (it != g_tc_shape.end()) return launch(it->second.first, it->second.second);
   }
-  if (stages) return launch(stages);
   cudaEvent_t e0, e1;
   STBEM_CUDA(cudaEventCreate(&e0));
   STBEM_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_st = max_st;
+  std::pair<int, int> best_c = cand.back();
   bem_status st = BEM_OK;
-  for (int c = std::max(1, std::min(2, max_st)); c <= max_st && st == BEM_OK; ++c) {
-    if ((st = launch(c)) != BEM_OK) break;   // warm-up
+  for (const auto& c : cand) {
+    if ((st = launch(c.first, c.second)) != BEM_OK) break;   // warm-up
     cudaEventRecord(e0, s);
-    if ((st = launch(c)) != BEM_OK) break;
+    if ((st = launch(c.first, c.second)) != BEM_OK) break;
     cudaEventRecord(e1, s);
     if (cudaEventSynchronize(e1) != cudaSuccess) {
       st = BEM_ERR_CUDA;
@@ -662,7 +887,7 @@ bem_status op_spmm_tc(const bem_operator* op, const double* x, double* y, int nr
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best) {
       best = ms;
-      best_st = c;
+      best_c = c;
     }
   }
   cudaEventDestroy(e0);
@@ -670,9 +895,9 @@ bem_status op_spmm_tc(const bem_operator* op, const double* x, double* y, int nr
   if (st != BEM_OK) return st;
   {
     std::lock_guard<std::mutex> lk(g_tc_mu);
-    g_tc_stages[key] = best_st;
+    g_tc_shape[key] = best_c;
   }
-  return launch(best_st);
+  return launch(best_c.first, best_c.second);
 }
 
 namespace {
