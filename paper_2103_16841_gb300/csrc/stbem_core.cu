@@ -774,7 +774,7 @@ __global__ void __launch_bounds__(kQuadThreads, STBEM_QUAD_MIN_CTAS) k_quad_bloc
 template <bool FP32>
 __global__ void __launch_bounds__(kQuadThreads, STBEM_QUAD_MIN_CTAS) k_quad_batch(const BlockCtx* __restrict__ Bs,
                                                        const int64_t* __restrict__ prefix, int S,
-                                                       unsigned long long* counter) {
+                                                       unsigned long long* counter, int64_t end) {
   typedef typename std::conditional<FP32, float, double>::type R;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ColSm C;
@@ -782,7 +782,7 @@ __global__ void __launch_bounds__(kQuadThreads, STBEM_QUAD_MIN_CTAS) k_quad_batc
   __shared__ BlockCtx sB;
   __shared__ int s_seg;
   int cur = -1;
-  const int64_t total = prefix[S];
+  const int64_t total = min(prefix[S], end);
   for (;;) {
     int64_t g = pop_block(counter);
     if (g >= total) break;
@@ -1035,14 +1035,31 @@ bem_status op_quadrature_batch(const std::vector<bem_operator*>& ops, BatchDev& 
   bem_status st = upload_batch(ops, dev, mt, ms, s);
   if (st != BEM_OK) return st;
   size_t smem = 0;
-  const int grid = quad_batch_grid(ops, smem);
+  const int max_grid = quad_batch_grid(ops, smem);
+  const int sms = (int)ops[0]->ctx->sm_count;
+  const int occ = std::max(1, max_grid / std::max(1, sms));
   const BlockCtx* d = static_cast<const BlockCtx*>(dev.d_ctx);
-  if (ops[0]->opts.precision == BEM_PREC_MIXED)
-    k_quad_batch<true><<<grid, kQuadThreads, smem, s>>>(d, dev.d_prefix, (int)ops.size(), dev.d_counter);
-  else
-    k_quad_batch<false><<<grid, kQuadThreads, smem, s>>>(d, dev.d_prefix, (int)ops.size(), dev.d_counter);
-  STBEM_CUDA(cudaGetLastError());
-  return BEM_OK;
+  auto launch = [&](int per, int64_t end) -> bem_status {
+    STBEM_CUDA(cudaMemsetAsync(dev.d_counter, 0, sizeof(unsigned long long), s));
+    const int grid = sms * std::max(1, std::min(per, occ));
+    if (ops[0]->opts.precision == BEM_PREC_MIXED)
+      k_quad_batch<true><<<grid, kQuadThreads, smem, s>>>(d, dev.d_prefix, (int)ops.size(), dev.d_counter, end);
+    else
+      k_quad_batch<false><<<grid, kQuadThreads, smem, s>>>(d, dev.d_prefix, (int)ops.size(), dev.d_counter, end);
+    STBEM_CUDA(cudaGetLastError());
+    return BEM_OK;
+  };
+  int64_t total = 0;
+  for (const bem_operator* op : ops) total += op->mesh->n_col * op->mesh->n_col;
+  int per = occ, how = 0;
+  if (ops[0]->ctx->tune_mode) {
+    // the batch's own shape class; sample: 1/32 of the block queue
+    const std::string key = batch_shape_class(ops[0]->ctx, ops[0]->opts.precision, ops[0]->nq, ops[0]->n_theta, mt,
+                                              ms, (int64_t)ops.size(), total);
+    st = tune_launch_shape(ops[0]->ctx, key, occ, std::max<int64_t>(total / 32, 1), launch, s, &per, &how, nullptr);
+    if (st != BEM_OK) return st;
+  }
+  return launch(per, total);
 }
 
 size_t block_ctx_size() { return sizeof(BlockCtx); }

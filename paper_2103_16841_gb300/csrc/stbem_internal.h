@@ -135,6 +135,12 @@ bem_status quad_launch(const bem_operator* op, int per_sm, int64_t end, const do
                        cudaStream_t s);
 // sets op->quad_per_sm: the context's tuning cache, a timed choice, or the default (stbem_tune.cu)
 bem_status choose_quad_shape(bem_operator* op, cudaStream_t s);
+// the tuner behind it: CTAs per SM for a launch(per_sm, end) over a sample of a block queue
+bem_status tune_launch_shape(const bem_context* ctx, const std::string& key, int occ, int64_t end,
+                             const std::function<bem_status(int, int64_t)>& launch, cudaStream_t s, int* per,
+                             int* how, double* ms_out);
+std::string batch_shape_class(const bem_context* ctx, int prec, int nq, int n_theta, int max_tet, int max_surf,
+                              int64_t n_ops, int64_t n_blocks);
 // raise a kernel's dynamic shared-memory limit to at least `bytes` (never lowers it)
 bem_status ensure_smem_attr(const void* kern, size_t bytes);
 // matrix-free product (internal order): the quadrature pass summed against x

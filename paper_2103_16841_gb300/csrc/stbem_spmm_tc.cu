@@ -84,6 +84,10 @@ namespace {
 constexpr long long kWaitBudget = 4000000000LL;   // clock cycles (about 2 s) per wait
 constexpr int kThreads = 192;
 constexpr int kMaxStages = 6;
+// after the stages: 3 mbarriers per stage and one more, the tensor-memory
+// address and the abort flag
+constexpr size_t kTailBytes = 256;
+static_assert(8 * (3 * kMaxStages + 1) + 8 <= kTailBytes, "stage tail");
 constexpr uint32_t kRsBytes = 1024;   // per stage: row starts (<= 784 bytes) and the block record
 constexpr uint32_t kMetaOff = 896;
 
@@ -806,7 +810,7 @@ bem_status op_spmm_tc(const bem_operator* op, const double* x, double* y, int nr
   // shared memory per stage: A tile (kind 0 only), B tile, value slots, row starts
   const size_t stage_b = (size_t)nkc * N * 16 + v_bytes + kRsBytes;
   const size_t stage_a = (size_t)nkc * MT * 128 * 16;
-  const size_t tail = 128;   // mbarriers, tensor-memory address, abort flag
+  const size_t tail = kTailBytes;
   size_t smem_max = 0;
   {
     int dev = 0, v = 0;

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 #include <fstream>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <set>
@@ -49,6 +50,24 @@ std::string shape_class(const bem_operator* op) {
   return k.str();
 }
 
+}  // namespace
+
+std::string batch_shape_class(const bem_context* ctx, int prec, int nq, int n_theta, int max_tet, int max_surf,
+                              int64_t n_ops, int64_t n_blocks) {
+  cudaDeviceProp p;
+  std::string name = "device";
+  if (cudaGetDeviceProperties(&p, ctx->device) == cudaSuccess) name = p.name;
+  for (char& c : name)
+    if (c == ' ' || c == '|') c = '_';
+  std::ostringstream k;
+  k << name << "|sm" << (int)ctx->sm_count << "|batch|p" << prec << "|q" << nq << "|t" << n_theta << "|r" << max_tet
+    << "|f" << max_surf << "|o" << (int)std::floor(std::log2((double)std::max<int64_t>(n_ops, 1))) << "|b"
+    << (int)std::floor(std::log2((double)std::max<int64_t>(n_blocks, 1)));
+  return k.str();
+}
+
+namespace {
+
 void read_cache(const std::string& path) {
   if (path.empty() || g_read.count(path)) return;
   g_read.insert(path);
@@ -70,35 +89,29 @@ void append_cache(const std::string& path, const std::string& key, int per) {
 
 }  // namespace
 
-bem_status choose_quad_shape(bem_operator* op, cudaStream_t s) {
-  if (op->quad_per_sm > 0) return BEM_OK;
-  const int occ = quad_max_per_sm(op);
-  if (op->ctx->tune_mode == 0 || op->opts.matrix_free) {
-    op->quad_per_sm = occ;
-    op->quad_tuned = 0;
-    return BEM_OK;
-  }
-  const std::string key = shape_class(op);
+// Times launch(per_sm, end) for per_sm = occ - 2 .. occ on the sample
+// [0, end) after one warm-up launch; *per = the fastest, ms[per - 1] its
+// sample times (how = 1), or the class's cached choice (how = 2).
+bem_status tune_launch_shape(const bem_context* ctx, const std::string& key, int occ, int64_t end,
+                             const std::function<bem_status(int, int64_t)>& launch, cudaStream_t s, int* per,
+                             int* how, double* ms_out) {
   std::lock_guard<std::mutex> lk(g_mu);   // one tuning at a time (and a quiet device for it)
-  read_cache(op->ctx->tune_path);
+  read_cache(ctx->tune_path);
   auto it = g_shape.find(key);
   if (it != g_shape.end()) {
-    op->quad_per_sm = std::min(it->second, occ);
-    op->quad_tuned = 2;
+    *per = std::min(it->second, occ);
+    *how = 2;
     return BEM_OK;
   }
-  // sample: 1/32 of the dense block order, at least 16 test columns
-  const int64_t nblk = op->mesh->n_col * op->mesh->n_col;
-  const int64_t end = std::min(nblk, std::max(nblk / 32, 16 * op->mesh->n_col));
   cudaEvent_t e0, e1;
   STBEM_CUDA(cudaEventCreate(&e0));
   STBEM_CUDA(cudaEventCreate(&e1));
-  bem_status st = quad_launch(op, occ, end, nullptr, nullptr, 0, s);   // warm-up
+  bem_status st = launch(occ, end);   // warm-up
   int best = occ;
   float best_ms = 1e30f;
-  for (int per = std::max(1, occ - 2); per <= occ && st == BEM_OK; ++per) {
+  for (int p = std::max(1, occ - 2); p <= occ && st == BEM_OK; ++p) {
     cudaEventRecord(e0, s);
-    st = quad_launch(op, per, end, nullptr, nullptr, 0, s);
+    st = launch(p, end);
     cudaEventRecord(e1, s);
     if (st != BEM_OK) break;
     if (cudaEventSynchronize(e1) != cudaSuccess) {
@@ -108,20 +121,36 @@ bem_status choose_quad_shape(bem_operator* op, cudaStream_t s) {
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    if (per - 1 < 8) op->tune_ms[per - 1] = ms;
+    if (ms_out && p - 1 < 8) ms_out[p - 1] = ms;
     if (ms < best_ms) {
       best_ms = ms;
-      best = per;
+      best = p;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != BEM_OK) return st;
   g_shape[key] = best;
-  append_cache(op->ctx->tune_path, key, best);
-  op->quad_per_sm = best;
-  op->quad_tuned = 1;
+  append_cache(ctx->tune_path, key, best);
+  *per = best;
+  *how = 1;
   return BEM_OK;
+}
+
+bem_status choose_quad_shape(bem_operator* op, cudaStream_t s) {
+  if (op->quad_per_sm > 0) return BEM_OK;
+  const int occ = quad_max_per_sm(op);
+  if (op->ctx->tune_mode == 0 || op->opts.matrix_free) {
+    op->quad_per_sm = occ;
+    op->quad_tuned = 0;
+    return BEM_OK;
+  }
+  // sample: 1/32 of the dense block order, at least 16 test columns
+  const int64_t nblk = op->mesh->n_col * op->mesh->n_col;
+  const int64_t end = std::min(nblk, std::max(nblk / 32, 16 * op->mesh->n_col));
+  auto launch = [&](int per, int64_t e) { return quad_launch(op, per, e, nullptr, nullptr, 0, s); };
+  return tune_launch_shape(op->ctx, shape_class(op), occ, end, launch, s, &op->quad_per_sm, &op->quad_tuned,
+                           op->tune_ms);
 }
 
 }  // namespace stbem
