@@ -177,6 +177,43 @@ def aggregate(ms, pairs, device):
     return float(t.item()), float(n.item())
 
 
+def product_only(args):
+    """Profiling aid: the tensor-core product of 64 right-hand sides on the
+    workload's mixed operator, timed with CUDA events after the shape tuning;
+    one more product runs between cudaProfilerStart/Stop (for ncu
+    --profile-from-start off). Prints one JSON line."""
+    import torch
+    import paper_2103_16841_gb300 as stb
+    from paper_2103_16841_gb300 import inputs
+    m = {"c2": inputs.workload_c2, "l3x16": lambda: inputs.sphere_mesh(3, 16, 4.0, 0.2, seed=1),
+         "l3x8": lambda: inputs.sphere_mesh(3, 8, 4.0, 0.2, seed=1),
+         "l2x8": lambda: inputs.sphere_mesh(2, 8, 2.0, 0.2, seed=3)}[args.workload]()
+    ctx = stb.Context(0)
+    op = stb.Operator(ctx, stb.Mesh.from_spacetime(ctx, m), "mixed")
+    g = torch.Generator(device="cuda").manual_seed(3)
+    x = 0.5 + 0.5 * torch.rand((64, m.n_tet), dtype=torch.float64, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    dt = args.product_only
+    op.matvec(x, y=y, dtype=dt)   # tunes the launch shape
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        op.matvec(x, y=y, dtype=dt)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 5
+    torch.cuda.profiler.start()
+    op.matvec(x, y=y, dtype=dt)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    st = op.stats()
+    print(json.dumps({"workload": WORKLOADS[args.workload], "dtype": dt, "nrhs": 64, "ms_per_product": ms,
+                      "stored_values": st["stored"],
+                      "note": "bem_matvec_dtype from device arrays in caller order (permutations and packing "
+                              "included)"}), flush=True)
+
+
 def run_ours(args):
     import torch
     import paper_2103_16841_gb300 as stb
@@ -305,7 +342,7 @@ def run_ours(args):
                    "l2": f"each step writes the {vbytes / 1e9:.2f} GB value array: "
                          + ("larger than L2" if vbytes > L2_BYTES else "smaller than L2 (profiling case)")},
         "phases_ms": {k: round(float(np.mean([p[k] for p in phases])), 2) for k in phases[0]},
-        "e2e": {"value": total_pairs / t_e2e, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
+        "e2e": None if not e2e_times else {"value": total_pairs / t_e2e, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "seconds_per_step": t_e2e,
                 "includes": "mesh upload, assembly, RHS, GMRES(FP32 inner + FP64 refinement, tol 1e-8), "
                             "density to host",
@@ -592,10 +629,16 @@ def main():
     ap.add_argument("--serve-small", dest="serve_full", action="store_false",
                     help="draw from levels 1-2 and 8/16 slabs only (default: the full mix, levels 1-3 x 8/16/32 "
                          "slabs x 1/4/16 RHS)")
+    ap.add_argument("--product-only", dest="product_only", default=None, choices=["tf32", "bf16", "fp32"],
+                    help="profiling aid: time the 64-RHS product of the workload's operator in this arithmetic "
+                         "and run one more under cudaProfilerStart/Stop, then exit")
     ap.add_argument("--workload", default="c2", choices=["c2", "l3x16", "l3x8", "l2x8"],
                     help="l3x16 / l3x8 / l2x8: the level-3 sphere with 16 or 8 slabs (T = 4) / the level-2 sphere "
                          "with 8 slabs (T = 2), jittered, for profiler captures only")
     args = ap.parse_args()
+    if args.product_only:
+        product_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
