@@ -1,0 +1,82 @@
+"""Convergence study of the indirect BEM on the unit sphere with zonal data
+(Sec. 4.3, experiment 3): g = g0(t) Re Y_1^0(x), g0 = t^4 exp(-2t), exact
+solution w = w0(t) Re Y_1^0(x) with w0 from the 1D Volterra equation of
+tests/_volterra.py (Re Y_1^0 is proportional to x3 on the sphere; the
+constant cancels in the relative errors). The data are sampled at the
+library's face quadrature points (bem_rhs_from_samples); e_BEM and e_opt of
+eq. err_l2 over icosphere levels 1-3 at a fixed ratio of time step to mesh
+width, T = 4 (the paper also runs T = 8, 16)."""
+import math
+
+import numpy as np
+import pytest
+
+from _volterra import solve_zonal
+from paper_2103_16841_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def dg0(t):
+    t = np.asarray(t, dtype=float)
+    return np.where(t > 0, (4 * t ** 3 - 2 * t ** 4) * np.exp(-2 * t), 0.0)
+
+
+def g0(t):
+    t = np.asarray(t, dtype=float)
+    return np.where(t > 0, t ** 4 * np.exp(-2 * t), 0.0)
+
+
+def zonal(x):
+    """x3 / |x|: Re Y_1^0 up to its constant, at the radial projection onto the sphere."""
+    return x[..., 2] / np.linalg.norm(x, axis=-1)
+
+
+def errors(m, w, t_grid, w_grid):
+    """(e_BEM, e_opt, e_abs) of eq. err_l2 with the degree-2 four-point
+    tetrahedral rule per panel; the L2 projection onto S_h^0 is the panel mean."""
+    X = m.stv_xyzt()
+    T = X[m.tets]                                    # [n, 4, 4] (t, x, y, z)
+    E = T[:, 1:, :] - T[:, :1, :]
+    vol = np.sqrt(np.maximum(np.linalg.det(E @ np.transpose(E, (0, 2, 1))), 0.0)) / 6.0
+    a, bq = 0.5854101966249685, 0.1381966011250105
+    L = np.full((4, 4), bq) + np.eye(4) * (a - bq)
+    Q = np.einsum("qk,nkd->nqd", L, T)               # [n, 4, 4] quadrature nodes
+    ex = np.interp(Q[..., 0], t_grid, w_grid) * zonal(Q[..., 1:])
+    wq = vol[:, None] / 4
+    ref2 = np.sum(wq * ex ** 2)
+    err2 = np.sum(wq * (ex - w[:, None]) ** 2)
+    mean = ex.mean(axis=1)
+    opt2 = np.sum(wq * (ex - mean[:, None]) ** 2)
+    return math.sqrt(err2 / ref2), math.sqrt(opt2 / ref2), math.sqrt(err2)
+
+
+def test_sphere_zonal_convergence():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2103_16841_gb300 as stb
+    ctx = stb.Context(0)
+    T = 4.0
+    t_grid, w_grid = solve_zonal(1, dg0, T, M=4000)
+    rows = []
+    for level, slabs in [(1, 8), (2, 16), (3, 32)]:
+        m = inputs.sphere_mesh(level, slabs, T, 0.0)
+        mesh = stb.Mesh.from_spacetime(ctx, m)
+        op = stb.Operator(ctx, mesh, "mixed")
+        pts, _ = op.rhs_points(1, 4)
+        g = g0(pts[:, 0]) * zonal(pts[:, 1:])
+        b = op.rhs_from_samples(g, 1, 4)
+        w, info = op.solve(b, tol=1e-10, restart=100, maxit=4000, inner="fp32", max_refine=12)
+        assert info[0]["converged"]
+        rows.append(errors(m, w, t_grid, w_grid))
+        op.close()
+        mesh.close()
+    e_bem = [r[0] for r in rows]
+    e_opt = [r[1] for r in rows]
+    print("levels 1-3, T = 4: e_BEM", e_bem, "e_opt", e_opt, "e_abs", [r[2] for r in rows])
+    # first order in h for both, and quasi-optimality e_BEM <= C(T) e_opt
+    for e in (e_bem, e_opt):
+        assert e[1] < e[0] and e[2] < e[1]
+        assert e[2] < 0.6 * e[0]
+    assert max(b / o for b, o in zip(e_bem, e_opt)) < 4.0
