@@ -196,11 +196,15 @@ bem_status bem_operator_stats(const bem_operator* op, int64_t* nnz_pattern, int6
  * (a face shared by two test panels counted once). Counted by the pattern pass. */
 bem_status bem_operator_work(const bem_operator* op, int64_t* inner_integrals);
 
-/* The quadrature's launch shape: CTAs per SM, how it was chosen (0 default,
- * 1 timed in this assembly, 2 taken from the tuning cache) and, when timed,
- * the sample time in ms of each candidate (index = CTAs per SM - 1; 0 where
- * not timed). Any pointer may be NULL; sample_ms has 8 entries. */
-bem_status bem_operator_tuning(const bem_operator* op, int* ctas_per_sm, int* tuned, double* sample_ms);
+/* The quadrature's launch shape: CTAs per SM, the CTAs per SM its register
+ * budget was compiled for (4: 128 registers; 2: 255, mixed precision only),
+ * how it was chosen (0 default, 1 timed in this assembly, 2 taken from the
+ * tuning cache) and, when timed, the sample time in ms of each candidate
+ * (index = 4 x (budget == 2) + CTAs per SM - 1; 0 where not timed). Untuned,
+ * the 2-CTA budget is taken where shared memory admits no more than 2 CTAs
+ * per SM anyway. Any pointer may be NULL; sample_ms has 8 entries. */
+bem_status bem_operator_tuning(const bem_operator* op, int* ctas_per_sm, int* budget_ctas, int* tuned,
+                               double* sample_ms);
 
 /* Scans the stored values on the device: number of non-finite values (NaN,
  * Inf) and the largest magnitude. A healthy operator has n_nonfinite = 0.

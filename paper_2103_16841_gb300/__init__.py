@@ -142,11 +142,13 @@ class Operator:
 
     def tuning(self):
         """The quadrature's launch shape (bem_operator_tuning)."""
-        per, how = ctypes.c_int(), ctypes.c_int()
+        per, budget, how = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         ms = np.zeros(8)
-        _lib.check(self.ctx._L.bem_operator_tuning(self.h, ctypes.byref(per), ctypes.byref(how), _lib.dptr(ms)))
-        return {"ctas_per_sm": per.value, "tuned": ["default", "timed", "cache"][how.value],
-                "sample_ms": {k + 1: float(v) for k, v in enumerate(ms) if v > 0}}
+        _lib.check(self.ctx._L.bem_operator_tuning(self.h, ctypes.byref(per), ctypes.byref(budget), ctypes.byref(how),
+                                                   _lib.dptr(ms)))
+        # candidate "b<budget>x<CTAs per SM>": its sample time
+        return {"ctas_per_sm": per.value, "budget_ctas": budget.value, "tuned": ["default", "timed", "cache"][how.value],
+                "sample_ms": {"b%dx%d" % (2 if k >= 4 else 4, k % 4 + 1): float(v) for k, v in enumerate(ms) if v > 0}}
 
     def check(self):
         """(number of non-finite stored values, largest |value|)"""

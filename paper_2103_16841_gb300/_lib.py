@@ -119,7 +119,8 @@ def load(build_if_missing: bool = False):
     L.bem_alu_peaks.argtypes = [VP, D, D]
     L.bem_context_set_tuning.argtypes = [VP, ctypes.c_int, ctypes.c_char_p]
     L.bem_selftest_bounded_wait.argtypes = [VP, D]
-    L.bem_operator_tuning.argtypes = [VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), D]
+    L.bem_operator_tuning.argtypes = [VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), D]
     L.bem_context_destroy.restype = None
     L.bem_mesh_create.argtypes = [VP, ctypes.c_int64, D, ctypes.c_int64, I32, D, ctypes.c_int64, I32,
                                   ctypes.POINTER(VP)]

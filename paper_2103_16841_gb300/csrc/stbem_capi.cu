@@ -374,7 +374,7 @@ bem_status stbem::op_layout(bem_operator* op, const int32_t* bw, const int64_t* 
     op->nstored = vo; op->nrows_stored = ro; op->nnz = nnz; op->nblocks = nblk;
     op->max_bw = wmax;
     if (own_scratch) {
-      const int64_t grid = (int64_t)op->ctx->sm_count * quad_max_per_sm(op);
+      const int64_t grid = (int64_t)op->ctx->sm_count * quad_max_per_sm(op, 0);
       op->tmp_len = std::max<int64_t>((int64_t)grid * m->max_col_surf * m->max_col_tets, 2 * m->n_tet * 8);
     } else {
       op->tmp_len = 0;

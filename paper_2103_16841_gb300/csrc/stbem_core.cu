@@ -745,20 +745,21 @@ __device__ __forceinline__ void quad_block(const BlockCtx& B, int64_t b, unsigne
   }
 }
 
-// CTAs of 128 threads resident per SM that the register budget is cut for
-// (quadrature of the level-3, 32-slab sphere in mixed precision: 4 / 5 / 6
-// CTAs took 6.83 / 6.91 / 7.56 s)
-#ifndef STBEM_QUAD_MIN_CTAS
-#define STBEM_QUAD_MIN_CTAS 4
-#endif
+// STBEM_QUAD_MIN_CTAS (stbem_internal.h): CTAs of 128 threads resident per
+// SM that the default register budget is cut for (quadrature of the level-3,
+// 32-slab sphere in mixed precision with an earlier build: 4 / 5 / 6 CTAs
+// took 6.83 / 6.91 / 7.56 s)
 // warps per quadrature CTA
 #ifndef STBEM_QUAD_WARPS
 #define STBEM_QUAD_WARPS 4
 #endif
 constexpr int kQuadThreads = 32 * STBEM_QUAD_WARPS;
 
-template <bool FP32>
-__global__ void __launch_bounds__(kQuadThreads, STBEM_QUAD_MIN_CTAS) k_quad_blocks(BlockCtx B) {
+// MINB: CTAs per SM the register budget is cut for (STBEM_QUAD_MIN_CTAS: 128
+// registers; 2: up to 255, no spills, for meshes whose shared memory per CTA
+// lets no more than 2 CTAs share an SM anyway)
+template <bool FP32, int MINB>
+__global__ void __launch_bounds__(kQuadThreads, MINB) k_quad_blocks(BlockCtx B) {
   typedef typename std::conditional<FP32, float, double>::type R;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ColSm C;
@@ -881,16 +882,24 @@ bem_status op_pattern(bem_operator* op, cudaStream_t s) {
   return BEM_OK;
 }
 
-int quad_max_per_sm(const bem_operator* op) {
+// quadrature kernel of a precision and register budget (variant 0: the
+// STBEM_QUAD_MIN_CTAS budget; variant 1: the 2-CTA budget, mixed precision only)
+static const void* quad_kernel(const bem_operator* op, int variant) {
+  if (op->opts.precision != BEM_PREC_MIXED) return (const void*)k_quad_blocks<false, STBEM_QUAD_MIN_CTAS>;
+  return variant ? (const void*)k_quad_blocks<true, 2> : (const void*)k_quad_blocks<true, STBEM_QUAD_MIN_CTAS>;
+}
+
+int quad_variants(const bem_operator* op) { return op->opts.precision == BEM_PREC_MIXED ? 2 : 1; }
+
+int quad_max_per_sm(const bem_operator* op, int variant) {
   const size_t smem = block_smem(op, true);
-  const void* kern = op->opts.precision == BEM_PREC_MIXED ? (const void*)k_quad_blocks<true>
-                                                          : (const void*)k_quad_blocks<false>;
+  const void* kern = quad_kernel(op, variant);
   ensure_smem_attr(kern, smem);
   return std::max(1, persistent_grid(kern, smem, kQuadThreads) / std::max(1, (int)op->ctx->sm_count));
 }
 
 bem_status quad_launch(const bem_operator* op, int per_sm, int64_t end, const double* mf_x, double* mf_y, int nrhs,
-                       cudaStream_t s) {
+                       cudaStream_t s, int variant) {
   BlockCtx B = make_ctx(const_cast<bem_operator*>(op));
   bem_status st = get_counter(op, &B.counter, s);
   if (st != BEM_OK) return st;
@@ -899,15 +908,17 @@ bem_status quad_launch(const bem_operator* op, int per_sm, int64_t end, const do
   B.mf_y = mf_y;
   B.mf_nrhs = nrhs;
   B.mf_ld = op->mesh->n_tet;
+  if (variant >= quad_variants(op)) variant = 0;
   const size_t smem = block_smem(op, true);
-  const int max_per = quad_max_per_sm(op);
+  const int max_per = quad_max_per_sm(op, variant);
   const int grid = (int)op->ctx->sm_count * std::max(1, std::min(per_sm, max_per));
   if ((int64_t)grid * op->mesh->max_col_surf * op->mesh->max_col_tets > op->tmp_len) {
     set_error("quadrature scratch too small");
     return BEM_ERR_INTERNAL;
   }
-  if (op->opts.precision == BEM_PREC_MIXED) k_quad_blocks<true><<<grid, kQuadThreads, smem, s>>>(B);
-  else k_quad_blocks<false><<<grid, kQuadThreads, smem, s>>>(B);
+  if (op->opts.precision != BEM_PREC_MIXED) k_quad_blocks<false, STBEM_QUAD_MIN_CTAS><<<grid, kQuadThreads, smem, s>>>(B);
+  else if (variant) k_quad_blocks<true, 2><<<grid, kQuadThreads, smem, s>>>(B);
+  else k_quad_blocks<true, STBEM_QUAD_MIN_CTAS><<<grid, kQuadThreads, smem, s>>>(B);
   STBEM_CUDA(cudaGetLastError());
   return BEM_OK;
 }
@@ -915,15 +926,17 @@ bem_status quad_launch(const bem_operator* op, int per_sm, int64_t end, const do
 bem_status op_quadrature(bem_operator* op, cudaStream_t s) {
   bem_status st = choose_quad_shape(op, s);
   if (st != BEM_OK) return st;
-  return quad_launch(op, op->quad_per_sm, op->mesh->n_col * op->mesh->n_col, nullptr, nullptr, 0, s);
+  return quad_launch(op, op->quad_per_sm, op->mesh->n_col * op->mesh->n_col, nullptr, nullptr, 0, s,
+                     op->quad_variant);
 }
 
 // Matrix-free product y = A x (internal order, [nrhs][n_tet]): the quadrature
 // pass with the entries summed against x instead of stored.
 bem_status op_matvec_free(const bem_operator* op, const double* x, double* y, int nrhs, cudaStream_t s) {
   STBEM_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * op->mesh->n_tet * nrhs, s));
-  const int per_sm = op->quad_per_sm > 0 ? op->quad_per_sm : quad_max_per_sm(op);
-  return quad_launch(op, per_sm, op->mesh->n_col * op->mesh->n_col, x, y, nrhs, s);
+  int per_sm = op->quad_per_sm, variant = op->quad_variant;
+  if (per_sm <= 0) default_quad_shape(op, &per_sm, &variant);
+  return quad_launch(op, per_sm, op->mesh->n_col * op->mesh->n_col, x, y, nrhs, s, variant);
 }
 
 // ---------------------------------------------------------------------------
@@ -1056,7 +1069,9 @@ bem_status op_quadrature_batch(const std::vector<bem_operator*>& ops, BatchDev& 
     // the batch's own shape class; sample: 1/32 of the block queue
     const std::string key = batch_shape_class(ops[0]->ctx, ops[0]->opts.precision, ops[0]->nq, ops[0]->n_theta, mt,
                                               ms, (int64_t)ops.size(), total);
-    st = tune_launch_shape(ops[0]->ctx, key, occ, std::max<int64_t>(total / 32, 1), launch, s, &per, &how, nullptr);
+    std::vector<int> codes;
+    for (int p = std::max(1, occ - 2); p <= occ; ++p) codes.push_back(p);
+    st = tune_launch_shape(ops[0]->ctx, key, codes, std::max<int64_t>(total / 32, 1), launch, s, &per, &how, nullptr);
     if (st != BEM_OK) return st;
   }
   return launch(per, total);

@@ -28,6 +28,10 @@ void set_error(const std::string& msg);
 constexpr int MAX_COL_TETS = 192;   // panels sharing one spatial triangle
 constexpr int MAX_COL_SURF = 193;   // nu_t != 0 faces over one spatial triangle
 constexpr int MAX_NQ = 64;          // m_Q^2 outer points per face
+#ifndef STBEM_QUAD_MIN_CTAS
+#define STBEM_QUAD_MIN_CTAS 4           // CTAs per SM the quadrature's default register budget is cut for
+#endif
+constexpr int STBEM_QUAD_BUDGET_CTAS = STBEM_QUAD_MIN_CTAS;
 
 // Per panel data on the device (internal panel order: by column, then time).
 struct TetDev {
@@ -94,8 +98,9 @@ struct bem_operator {
   double assemble_ms = 0.0;
   double phase_ms[4] = {0, 0, 0, 0};
   int quad_per_sm = 0;           // CTAs per SM of the persistent quadrature (0: not chosen yet)
+  int quad_variant = 0;          // its register budget (0: 4 CTAs per SM, 1: 2 CTAs per SM)
   int quad_tuned = 0;            // 0 default shape, 1 timed here, 2 from the tuning cache
-  double tune_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // sample time per candidate (CTAs per SM = index + 1)
+  double tune_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // sample time per candidate: index = 4 variant + CTAs per SM - 1
   unsigned long long* d_counter = nullptr;  // work counter of the persistent kernels
   // quadrature scratch
   double* d_tmp = nullptr;
@@ -127,18 +132,25 @@ bem_status mesh_device_geometry(bem_mesh* m, const double* d_sv_xyz, const int32
 bem_status op_outer_points(bem_operator* op, cudaStream_t s);
 bem_status op_pattern(bem_operator* op, cudaStream_t s);
 bem_status op_quadrature(bem_operator* op, cudaStream_t s);
-// most CTAs of the quadrature kernel resident per SM (shared memory and registers)
-int quad_max_per_sm(const bem_operator* op);
-// one persistent quadrature launch with per_sm CTAs per SM over the blocks
-// [0, end) of the dense (I, J) order (assembled, or summed against mf_x)
+// register-budget variants of the quadrature kernel (1 for FP64 operators;
+// 2 for mixed ones: the 4-CTA budget, and the 2-CTA budget of 255 registers)
+int quad_variants(const bem_operator* op);
+// most CTAs of a variant of the quadrature kernel resident per SM (shared memory and registers)
+int quad_max_per_sm(const bem_operator* op, int variant);
+// one persistent quadrature launch of a variant with per_sm CTAs per SM over
+// the blocks [0, end) of the dense (I, J) order (assembled, or summed against mf_x)
 bem_status quad_launch(const bem_operator* op, int per_sm, int64_t end, const double* mf_x, double* mf_y, int nrhs,
-                       cudaStream_t s);
+                       cudaStream_t s, int variant);
+// the untuned shape: the 2-CTA budget where shared memory admits no more than
+// 2 CTAs per SM anyway, else the 4-CTA budget; its occupancy
+void default_quad_shape(const bem_operator* op, int* per_sm, int* variant);
 // sets op->quad_per_sm: the context's tuning cache, a timed choice, or the default (stbem_tune.cu)
 bem_status choose_quad_shape(bem_operator* op, cudaStream_t s);
-// the tuner behind it: CTAs per SM for a launch(per_sm, end) over a sample of a block queue
-bem_status tune_launch_shape(const bem_context* ctx, const std::string& key, int occ, int64_t end,
-                             const std::function<bem_status(int, int64_t)>& launch, cudaStream_t s, int* per,
-                             int* how, double* ms_out);
+// the tuner behind it: the fastest of the candidate launch codes of launch(code, end)
+// over a sample [0, end) of a block queue (the code's meaning is the caller's)
+bem_status tune_launch_shape(const bem_context* ctx, const std::string& key, const std::vector<int>& codes,
+                             int64_t end, const std::function<bem_status(int, int64_t)>& launch, cudaStream_t s,
+                             int* best_code, int* how, double* ms_out);
 std::string batch_shape_class(const bem_context* ctx, int prec, int nq, int n_theta, int max_tet, int max_surf,
                               int64_t n_ops, int64_t n_blocks);
 // raise a kernel's dynamic shared-memory limit to at least `bytes` (never lowers it)

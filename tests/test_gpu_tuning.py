@@ -35,15 +35,18 @@ def test_tuning_records_and_reuses_the_launch_shape(tmp_path):
     op = stb.Operator(ctx, mesh, "mixed")
     t = op.tuning()
     assert t["tuned"] == "timed"
-    assert t["ctas_per_sm"] in t["sample_ms"]
-    assert t["sample_ms"][t["ctas_per_sm"]] == min(t["sample_ms"].values())
+    chosen = "b%dx%d" % (t["budget_ctas"], t["ctas_per_sm"])
+    assert chosen in t["sample_ms"] and len(t["sample_ms"]) >= 2
+    assert t["sample_ms"][chosen] == min(t["sample_ms"].values())
+    cache_code = 4 * (t["budget_ctas"] == 2) + t["ctas_per_sm"] - 1
     lines = cache.read_text().splitlines()
-    assert len(lines) == 1 and lines[0].startswith("stbem-tune-v1 ") and lines[0].endswith(" %d" % t["ctas_per_sm"])
+    assert len(lines) == 1 and lines[0].startswith("stbem-tune-v2 ") and lines[0].endswith(" %d" % cache_code)
     # the same class again on another context: from the cache, no timing
     ctx2 = stb.Context(0)
     ctx2.set_tuning(1, str(cache))
     op2 = stb.Operator(ctx2, stb.Mesh.from_spacetime(ctx2, m), "mixed")
-    assert op2.tuning()["tuned"] == "cache" and op2.tuning()["ctas_per_sm"] == t["ctas_per_sm"]
+    t2 = op2.tuning()
+    assert t2["tuned"] == "cache" and (t2["ctas_per_sm"], t2["budget_ctas"]) == (t["ctas_per_sm"], t["budget_ctas"])
     # an untuned operator: the build's shape, the same values
     ctx3 = stb.Context(0)
     op3 = stb.Operator(ctx3, stb.Mesh.from_spacetime(ctx3, m), "mixed")
@@ -58,5 +61,5 @@ def test_tuning_records_and_reuses_the_launch_shape(tmp_path):
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr
     t4 = json.loads(out.stdout.strip().splitlines()[-1])
-    assert t4["tuned"] == "cache" and t4["ctas_per_sm"] == t["ctas_per_sm"]
+    assert t4["tuned"] == "cache" and (t4["ctas_per_sm"], t4["budget_ctas"]) == (t["ctas_per_sm"], t["budget_ctas"])
     assert len(cache.read_text().splitlines()) == 1
