@@ -291,15 +291,18 @@ bem_status bem_rhs_from_samples(const bem_operator* op, int32_t level, int32_t n
 bem_status bem_matvec(const bem_operator* op, const double* x_dev, double* y_dev, int32_t nrhs, void* stream);
 
 /* y_dev = A x_dev in the arithmetic `dtype` (BEM_DTYPE_*), same layout as
- * bem_matvec. TF32 and BF16 run the block matvec on the tensor cores for up
- * to 64 right-hand sides per pass (the stored values are read once per pass);
- * FP32, TF32 need the FP32 values (MIXED operators, or store_fp32 = 1); BF16
- * makes a BF16 copy of the values on first use. The products keep packed
- * operands in a per-operator workspace (allocated on first use); the first
+ * bem_matvec. TF32 and BF16 run the block matvec on the 5th-generation tensor
+ * cores (tcgen05.mma, FP32 accumulation in tensor memory) for up to 64
+ * right-hand sides per pass (the values are read once per pass); FP32 and
+ * TF32 need the FP32 values (MIXED operators, or store_fp32 = 1). On first
+ * use the TF32 / BF16 products make the operator's block records and a copy
+ * of its values cut into 16-byte chunk slots in their type (1.1-1.25 x the
+ * value bytes, kept with the operator and remade after a reassembly); the
+ * products keep packed operands in a per-operator workspace; the first
  * TF32 / BF16 product of a mesh shape times the candidate launch shapes once
- * and keeps the fastest for the process (so that call synchronizes the
- * stream). Otherwise stream-ordered like bem_matvec: no allocation once the
- * workspaces have grown to the call's size, no synchronization. */
+ * and keeps the fastest for the process (so these first calls synchronize
+ * the stream). Otherwise stream-ordered like bem_matvec: no allocation once
+ * the workspaces have grown to the call's size, no synchronization. */
 bem_status bem_matvec_dtype(const bem_operator* op, const double* x_dev, double* y_dev, int32_t nrhs,
                             int32_t dtype, void* stream);
 
