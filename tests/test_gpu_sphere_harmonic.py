@@ -5,7 +5,7 @@ tests/_volterra.py (Re Y_1^0 is proportional to x3 on the sphere; the
 constant cancels in the relative errors). The data are sampled at the
 library's face quadrature points (bem_rhs_from_samples); e_BEM and e_opt of
 eq. err_l2 over icosphere levels 1-3 at a fixed ratio of time step to mesh
-width, T = 4 (the paper also runs T = 8, 16)."""
+width, T = 4, and levels 1-2 at T = 8 (the paper also runs T = 16)."""
 import math
 
 import numpy as np
@@ -52,15 +52,12 @@ def errors(m, w, t_grid, w_grid):
     return math.sqrt(err2 / ref2), math.sqrt(opt2 / ref2), math.sqrt(err2)
 
 
-def test_sphere_zonal_convergence():
-    if not torch.cuda.is_available():
-        pytest.skip("no GPU")
+def _study(T, levels):
     import paper_2103_16841_gb300 as stb
     ctx = stb.Context(0)
-    T = 4.0
     t_grid, w_grid = solve_zonal(1, dg0, T, M=4000)
     rows = []
-    for level, slabs in [(1, 8), (2, 16), (3, 32)]:
+    for level, slabs in levels:
         m = inputs.sphere_mesh(level, slabs, T, 0.0)
         mesh = stb.Mesh.from_spacetime(ctx, m)
         op = stb.Operator(ctx, mesh, "mixed")
@@ -74,9 +71,28 @@ def test_sphere_zonal_convergence():
         mesh.close()
     e_bem = [r[0] for r in rows]
     e_opt = [r[1] for r in rows]
-    print("levels 1-3, T = 4: e_BEM", e_bem, "e_opt", e_opt, "e_abs", [r[2] for r in rows])
+    print("T = %g, levels %s: e_BEM" % (T, [l for l, _ in levels]), e_bem, "e_opt", e_opt, "e_abs",
+          [r[2] for r in rows])
+    return e_bem, e_opt
+
+
+def test_sphere_zonal_convergence():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    e_bem, e_opt = _study(4.0, [(1, 8), (2, 16), (3, 32)])
     # first order in h for both, and quasi-optimality e_BEM <= C(T) e_opt
     for e in (e_bem, e_opt):
         assert e[1] < e[0] and e[2] < e[1]
         assert e[2] < 0.6 * e[0]
+    assert max(b / o for b, o in zip(e_bem, e_opt)) < 4.0
+
+
+def test_sphere_zonal_longer_time():
+    """T = 8 (the paper's second end time), levels 1-2: the same first-order
+    behaviour; the ratio e_BEM / e_opt (the constant C(T) of the paper's
+    quasi-optimality observation) is reported beside T = 4's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    e_bem, e_opt = _study(8.0, [(1, 16), (2, 32)])
+    assert e_bem[1] < 0.7 * e_bem[0] and e_opt[1] < 0.7 * e_opt[0]
     assert max(b / o for b, o in zip(e_bem, e_opt)) < 4.0
