@@ -516,6 +516,35 @@ bem_status bem_server_stats_get(const bem_server* srv, bem_server_stats* out);
 /* Finishes the queued and running requests, then frees everything. */
 void bem_server_destroy(bem_server* srv);
 
+/* ------------------------------------------------------------------ */
+/* Lit-panel search of Sec. 3.3 (host only, no device or context): a    */
+/* binary cluster tree over the panels (Def. bct) with a bounding ball  */
+/* per cluster, and the search ApproximateLitLeaves (Algorithm          */
+/* lit_leaves) with the ball test of Theorem phi_xi_sphere. It returns  */
+/* X_N(x), a superset of the panels whose support the backward light    */
+/* cone of x meets. The GPU path does not use it (it searches column    */
+/* windows with the same ball test per panel); it serves the            */
+/* cardinality study of Sec. 4.1.                                      */
+/* ------------------------------------------------------------------ */
+typedef struct bem_cluster_tree bem_cluster_tree;
+
+/* Panels as in bem_mesh_create_tets: vertices vert_txyz [n_vert][4]
+ * (t, x, y, z), panels tets [n_tet][4] (vertex ids). Leaves hold at most
+ * n_min >= 1 panels. Clusters split at the median of the panel centroids
+ * along the coordinate of largest extent; balls by Ritter's approximate
+ * bounding sphere in R^4 over the cluster's panel vertices. */
+bem_status bem_cluster_tree_create(int64_t n_vert, const double* vert_txyz, int64_t n_tet, const int32_t* tets,
+                                   int32_t n_min, bem_cluster_tree** out);
+/* Nodes, leaves and depth of the tree. Any pointer may be NULL. */
+bem_status bem_cluster_tree_info(const bem_cluster_tree* tree, int64_t* n_nodes, int64_t* n_leaves, int32_t* depth);
+/* X_N(x) for the point x_txyz [4]: the panels of the leaves the search
+ * keeps, in tree order, into panels [cap]; n_panels = their number (also
+ * when it exceeds cap, which returns BEM_ERR_INVALID_ARG), n_visited (may
+ * be NULL) = clusters whose ball was tested. */
+bem_status bem_cluster_tree_query(const bem_cluster_tree* tree, const double* x_txyz, int64_t cap, int32_t* panels,
+                                  int64_t* n_panels, int64_t* n_visited);
+void bem_cluster_tree_destroy(bem_cluster_tree* tree);
+
 #ifdef __cplusplus
 }
 #endif

@@ -523,3 +523,46 @@ def _stream_ptr(stream):
         stream = torch.cuda.current_stream()
     h = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     return ctypes.c_void_p(h if h else _CUDA_STREAM_LEGACY)
+
+
+class ClusterTree:
+    """bem_cluster_tree: the host-side lit-panel search of Sec. 3.3 (binary
+    cluster tree with bounding balls, Algorithm ApproximateLitLeaves). Needs
+    no GPU. m: a space-time mesh of inputs (vertices stv_xyzt(), panels tets)."""
+
+    def __init__(self, m, n_min=8):
+        L = _lib.load()
+        self._L = L
+        X = np.ascontiguousarray(m.stv_xyzt(), dtype=np.float64)
+        T = np.ascontiguousarray(m.tets, dtype=np.int32)
+        h = ctypes.c_void_p()
+        _lib.check(L.bem_cluster_tree_create(X.shape[0], _lib.dptr(X), T.shape[0], _lib.iptr(T), int(n_min),
+                                             ctypes.byref(h)))
+        self.h = h
+        self.n_tet = T.shape[0]
+
+    def info(self):
+        a = np.zeros(2, dtype=np.int64)
+        d = np.zeros(1, dtype=np.int32)
+        _lib.check(self._L.bem_cluster_tree_info(self.h, _lib.lptr(a[0:1]), _lib.lptr(a[1:2]), _lib.iptr(d)))
+        return {"nodes": int(a[0]), "leaves": int(a[1]), "depth": int(d[0])}
+
+    def query(self, x):
+        """X_N(x) (panel ids, caller numbering) and the number of clusters tested."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        out = np.zeros(self.n_tet, dtype=np.int32)
+        n, v = np.zeros(1, dtype=np.int64), np.zeros(1, dtype=np.int64)
+        _lib.check(self._L.bem_cluster_tree_query(self.h, _lib.dptr(x), self.n_tet, _lib.iptr(out), _lib.lptr(n),
+                                                  _lib.lptr(v)))
+        return out[:int(n[0])].copy(), int(v[0])
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.bem_cluster_tree_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libstbem.so")
-SOURCES = ["stbem_core.cu", "stbem_matvec.cu", "stbem_solver.cu", "stbem_gmres.cu", "stbem_capi.cu", "stbem_noalloc.cu", "stbem_server.cu", "stbem_batch.cu", "stbem_peaks.cu", "stbem_spmm_tc.cu", "stbem_tune.cu"]
+SOURCES = ["stbem_core.cu", "stbem_matvec.cu", "stbem_solver.cu", "stbem_gmres.cu", "stbem_capi.cu", "stbem_noalloc.cu", "stbem_server.cu", "stbem_batch.cu", "stbem_peaks.cu", "stbem_spmm_tc.cu", "stbem_tune.cu", "stbem_littree.cu"]
 HEADERS = ["stbem_quad.cuh", "stbem_internal.h", "stbem_tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The quadrature translation unit: FP32 division and square root to within a

@@ -35,6 +35,7 @@ EXPORTS = [
     "bem_batch_create", "bem_batch_stats", "bem_batch_solve", "bem_batch_destroy",
     "bem_server_create", "bem_server_submit", "bem_server_poll", "bem_server_release", "bem_server_stats_get",
     "bem_server_destroy",
+    "bem_cluster_tree_create", "bem_cluster_tree_info", "bem_cluster_tree_query", "bem_cluster_tree_destroy",
 ]
 
 
@@ -119,6 +120,11 @@ def load(build_if_missing: bool = False):
     L.bem_alu_peaks.argtypes = [VP, D, D]
     L.bem_context_set_tuning.argtypes = [VP, ctypes.c_int, ctypes.c_char_p]
     L.bem_selftest_bounded_wait.argtypes = [VP, D]
+    L.bem_cluster_tree_create.argtypes = [ctypes.c_int64, D, ctypes.c_int64, I32, ctypes.c_int32, ctypes.POINTER(VP)]
+    L.bem_cluster_tree_info.argtypes = [VP, I64, I64, I32]
+    L.bem_cluster_tree_query.argtypes = [VP, D, ctypes.c_int64, I32, I64, I64]
+    L.bem_cluster_tree_destroy.argtypes = [VP]
+    L.bem_cluster_tree_destroy.restype = None
     L.bem_operator_tuning.argtypes = [VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int), D]
     L.bem_context_destroy.restype = None
@@ -173,7 +179,8 @@ def load(build_if_missing: bool = False):
     L.bem_server_destroy.restype = None
     for name in EXPORTS:
         if name not in ("bem_context_destroy", "bem_mesh_destroy", "bem_operator_destroy", "bem_last_error",
-                        "bem_version", "bem_server_destroy", "bem_batch_destroy", "bem_request_destroy"):
+                        "bem_version", "bem_server_destroy", "bem_batch_destroy", "bem_request_destroy",
+                        "bem_cluster_tree_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
