@@ -81,3 +81,17 @@ def test_cardinality_study():
     # X_N is a bounded multiple of the lit set, and the search touches far fewer clusters than panels
     assert x1 <= 4.0 * l1 and x2 <= 4.0 * l2
     assert v3 < 0.25 * N3
+
+
+def test_rejects_bad_input():
+    import paper_2103_16841_gb300 as stb
+    m = inputs.sphere_mesh(0, 2, 1.0, 0.0)
+    with pytest.raises(stb.BemError) as e:
+        stb.ClusterTree(m, n_min=0)
+    assert e.value.status == 1
+    bad = inputs.sphere_mesh(0, 2, 1.0, 0.0)
+    bad.tets = bad.tets.copy()
+    bad.tets[0, 0] = 10 ** 6                                # vertex id out of range
+    with pytest.raises(stb.BemError) as e:
+        stb.ClusterTree(bad, n_min=4)
+    assert e.value.status == 1
