@@ -297,7 +297,8 @@ def run_ours(args):
     d2h = m.n_tet * 8 + m.n_tet * 8  # rhs vector and density back to the host
 
     acc = accuracy_leg(ctx, mesh, op, m, args) if (args.accuracy and rank == 0) else None
-    multi = multi_rhs_leg(op, m, args, ref=acc.pop("_W64") if acc else None) if args.multi_rhs > 0 else None
+    multi = (multi_rhs_leg(op, m, args, ref=acc.pop("_W64") if acc else None)
+             if (args.multi_rhs > 0 and rank == 0) else None)
     serving = serving_leg(ctx, args) if (args.serve_requests > 0 and rank == 0) else None
     batched = batch_leg(ctx, args) if (args.batch > 0 and rank == 0) else None
 
