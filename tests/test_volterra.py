@@ -4,6 +4,7 @@ experiment 3)."""
 import math
 
 import numpy as np
+import pytest
 
 from _volterra import apply_zonal, legendre, solve_zonal
 
@@ -41,13 +42,14 @@ def test_zonal_solution_satisfies_the_first_kind_equation():
         assert err <= 2e-5, (n, err)
 
 
-def test_funk_hecke_reduction_by_surface_quadrature():
-    """V(w0 P_1(x3))(t, x) computed as a surface integral over the unit sphere
+@pytest.mark.parametrize("n", [1, 2])
+def test_funk_hecke_reduction_by_surface_quadrature(n):
+    """V(w0 P_n(x3))(t, x) computed as a surface integral over the unit sphere
     (polar coordinates about x: |x - y| = 2 sin(theta/2), dA = sin(theta)
-    dtheta dphi, so the 1/r of the kernel cancels) equals P_1(x3) times the
+    dtheta dphi, so the 1/r of the kernel cancels) equals P_n(x3) times the
     left side of (V1): the reduction behind the reference, checked by brute
     force at a few (t, x)."""
-    t_grid, w = solve_zonal(1, dg0, 6.0, M=4000)
+    t_grid, w = solve_zonal(n, dg0, 6.0, M=4000)
     th, wt = np.polynomial.legendre.leggauss(400)
     th = 0.5 * math.pi * (th + 1.0)
     wt = 0.5 * math.pi * wt
@@ -60,7 +62,7 @@ def test_funk_hecke_reduction_by_surface_quadrature():
         y3 = x[2] * np.cos(T) + np.sin(T) * (np.cos(P) * u[2] + np.sin(P) * v[2])
         r = 2.0 * np.sin(0.5 * T)
         wv = np.interp(t - r, t_grid, w, left=0.0)
-        integrand = wv * y3 * np.cos(0.5 * T) / (4 * math.pi)
+        integrand = wv * legendre(n, y3) * np.cos(0.5 * T) / (4 * math.pi)
         surf = np.sum(wt[:, None] * integrand) * (2 * math.pi / len(ph))
-        red = legendre(1, x[2]) * apply_zonal(1, t_grid, w, [t], nodes=400)[0]
+        red = legendre(n, x[2]) * apply_zonal(n, t_grid, w, [t], nodes=400)[0]
         assert abs(surf - red) <= 1e-6 * max(1.0, abs(red)), (alpha, t, surf, red)
